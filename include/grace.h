@@ -1,0 +1,168 @@
+/*
+ * grace.h - C ABI of the GB300 (sm_103a) LLG hot path of Zhu, "Grace: a cross-platform
+ * micromagnetic simulator on graphics processing units" (arXiv:1411.2565).
+ *
+ * One step of the method (Sec. 2 and Sec. 3 of the paper):
+ *   H_eff = H_demag + H_exch + H_anis + H_ext                      (Eq. 2)
+ *     H_demag: zero-padded FFT convolution of M = Ms m with the cell-averaged demag
+ *              tensor (Sec. 3, with the paper's ref. [3], Newell et al. 1993)
+ *     H_exch : six-neighbour exchange (Sec. 3), free boundaries
+ *     H_anis : uniaxial anisotropy along x (Eq. 1)
+ *     H_ext  : Zeeman term (Eq. 1)
+ *   dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)]         (Eq. 3, gamma0 = mu0 gamma)
+ *   m_{n+1} = normalise(m_n + dt dm/dt)                             (explicit Euler, Sec. 3)
+ *
+ * Conventions for every entry point:
+ *   - Fields are FP32 structure-of-arrays [3][nz][ny][nx] (x fastest), SI units:
+ *     H in A/m, lengths in metres, time in seconds, energies in joules.
+ *   - A batch of films concatenates the per-film arrays in film order.
+ *   - "dev_" pointers are CUDA device pointers; "host_" pointers are host memory;
+ *     double[3] arguments are host memory.
+ *   - Ownership: the library owns only the opaque host handle.  It never allocates
+ *     device memory: the caller supplies one workspace (grace_bind) and every I/O
+ *     buffer, keeps them alive until grace_destroy (or until the pointer is replaced),
+ *     and supplies the CUDA stream all work is queued on.
+ *   - Errors: every call returns a grace_status; no exception or abort crosses the
+ *     ABI.  grace_last_error() describes the last failure of that handle.  Work is
+ *     asynchronous on the bound stream; a kernel fault surfaces as GRACE_ECUDA at the
+ *     next call that synchronises (grace_energy, grace_get_m_host) or checks launches.
+ */
+#ifndef GRACE_H_
+#define GRACE_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grace_ctx grace_ctx;
+
+typedef enum {
+  GRACE_OK = 0,
+  GRACE_EINVAL = -1,       /* bad argument: NULL, n_d < 1, n_d > 2048, cell <= 0, Ms <= 0, A < 0,
+                              alpha < 0, gamma0 <= 0, dt <= 0, n < 0, unknown option/term bits */
+  GRACE_EWORKSPACE = -2,   /* workspace smaller than grace_workspace_size or misaligned */
+  GRACE_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+  GRACE_ETIMEOUT = -4,     /* reserved: a bounded device-side wait expired */
+  GRACE_ESTATE = -5,       /* call out of order (e.g. step before bind / set_m) */
+  GRACE_ENONFINITE = -6,   /* a NaN or Inf appeared in <m> (checked by grace_energy) */
+  GRACE_EUNSUPPORTED = -7  /* valid arguments outside what this build supports */
+} grace_status;
+
+/* Term bits for grace_heff (Eq. 2). */
+enum {
+  GRACE_TERM_DEMAG = 1,
+  GRACE_TERM_EXCH = 2,
+  GRACE_TERM_ANIS = 4,
+  GRACE_TERM_ZEEMAN = 8,
+  GRACE_TERM_ALL = 15
+};
+
+/* Options for grace_set_option. */
+enum {
+  GRACE_OPT_GRAPH = 1,        /* 1 (default): grace_step replays captured CUDA graphs; 0: plain launches */
+  GRACE_OPT_GRAPH_STEPS = 2   /* steps per captured graph (even, >= 2; default 16) */
+};
+
+/*
+ * grace_create - plan one rectangular film (Sec. 2: regular cell grid; Sec. 4 workloads).
+ *   grid[3]   cells (nx, ny, nz), each 1..2048.
+ *   cell_m[3] cell size (dx, dy, dz) in metres, > 0.
+ *   Ms        saturation magnetisation (A/m, > 0); a per-cell field may replace it
+ *             (grace_set_ms_field).
+ *   A         exchange constant (J/m, >= 0), Eq. 1.
+ *   Ku        uniaxial anisotropy constant along x (J/m^3), Eq. 1.
+ *   alpha     damping (>= 0), gamma0 = mu0 gamma (m/(A s), > 0), Eq. 3.
+ * Each axis is zero-padded to P_d = smallest power of two >= 2 n_d - 1 (P_d = 1 when
+ * n_d = 1).  *out receives a new handle (NULL on failure).
+ */
+int grace_create(grace_ctx **out, const int grid[3], const double cell_m[3], double Ms,
+                 double A, double Ku, double alpha, double gamma0);
+
+/*
+ * grace_batch_create - plan nfilms independent films stepped together (one grouped launch
+ * per kernel for the whole ensemble).  Arrays hold nfilms entries (grid and cell_m: 3 per
+ * film, row-major).  Films with the same (grid, cell) share one demag tensor.
+ * Same validation as grace_create for every film; nfilms in 1..65536.
+ */
+int grace_batch_create(grace_ctx **out, int nfilms, const int *grid, const double *cell_m,
+                       const double *Ms, const double *A, const double *Ku,
+                       const double *alpha, const double *gamma0);
+
+/* Bytes of device workspace grace_bind needs (tensor, spectra, state, scratch). */
+int grace_workspace_size(const grace_ctx *ctx, size_t *bytes);
+
+/* Total number of cells over all films (N = sum nx ny nz). */
+int grace_ncells(const grace_ctx *ctx, long long *n);
+
+/*
+ * grace_bind - attach the caller's device workspace (>= grace_workspace_size bytes,
+ * 256-byte aligned) and CUDA stream (cudaStream_t, may be 0), then build the demag
+ * tensor spectrum on the device: Newell's FP64 closed form within 24 cells (Chebyshev
+ * distance), dipole plus second-order cell-shape term beyond, transformed in FP64 and
+ * stored FP32.  Must precede every other call except the queries above.
+ */
+int grace_bind(grace_ctx *ctx, void *dev_ws, size_t bytes, void *cuda_stream);
+
+/* Copy unit vectors m ([3][nz][ny][nx] per film, N*3 floats) in / out of the state. */
+int grace_set_m(grace_ctx *ctx, const float *dev_m);
+int grace_get_m(const grace_ctx *ctx, float *dev_m);
+/* Host-memory variants: the copy is queued on the bound stream; grace_get_m_host
+ * synchronises the stream before returning, so host_m is valid on return. */
+int grace_set_m_host(grace_ctx *ctx, const float *host_m);
+int grace_get_m_host(grace_ctx *ctx, float *host_m);
+
+/* Uniform applied field H_ext (A/m), Eq. 1 Zeeman term; all films, or one film. */
+int grace_set_hext(grace_ctx *ctx, const double h_Apm[3]);
+int grace_set_film_hext(grace_ctx *ctx, int film, const double h_Apm[3]);
+/* Per-cell applied field (device, 3*N floats, A/m) added to the uniform one; NULL clears. */
+int grace_set_hext_field(grace_ctx *ctx, const float *dev_h);
+/* Per-cell saturation magnetisation (device, N floats, A/m, > 0); NULL restores the
+ * uniform Ms.  The observer cell's Ms enters the exchange and anisotropy prefactors. */
+int grace_set_ms_field(grace_ctx *ctx, const float *dev_ms);
+
+/*
+ * grace_heff - H_eff of the current state restricted to term_mask (Eq. 2), written to
+ * dev_h (3*N floats).  The state is unchanged.
+ */
+int grace_heff(grace_ctx *ctx, float *dev_h, unsigned term_mask);
+
+/* grace_step - n explicit Euler steps of Eq. 3 with renormalisation, time step dt_s. */
+int grace_step(grace_ctx *ctx, int n, double dt_s);
+
+/*
+ * grace_energy - FP64 energies of the current state (Eq. 1 times the cell volume):
+ * out[0..4] = {E_exch, E_anis, E_demag, E_zeeman, E_total}, summed over all films, and
+ * mavg[3] = <m> over all cells.  Either pointer may be NULL.  Synchronises the stream;
+ * returns GRACE_ENONFINITE if <m> is not finite.
+ */
+int grace_energy(grace_ctx *ctx, double out[5], double mavg[3]);
+
+/*
+ * grace_backward - discrete adjoint of n Euler steps from the current state m_0 for a
+ * loss whose gradient with respect to m_n is dev_dL_dmT (3*N floats).  Replays the
+ * forward steps from checkpoints taken every ckpt_every steps (recompute between).
+ * Accumulates (adds into) dev_dL_dhext (3*N, gradient w.r.t. a per-cell applied field)
+ * and dev_dL_dms (N, gradient w.r.t. a per-cell Ms) when non-NULL, and writes dL/dm_0
+ * to dev_dL_dm0 when non-NULL.  The state is left at m_0.  Needs
+ * grace_backward_workspace_size() bytes in dev_scratch.
+ */
+int grace_backward_workspace_size(const grace_ctx *ctx, int n, int ckpt_every, size_t *bytes);
+int grace_backward(grace_ctx *ctx, const float *dev_dL_dmT, int n, double dt_s, int ckpt_every,
+                   void *dev_scratch, size_t scratch_bytes, float *dev_dL_dhext,
+                   float *dev_dL_dms, float *dev_dL_dm0);
+
+/* grace_set_option - see GRACE_OPT_*. */
+int grace_set_option(grace_ctx *ctx, int option, long long value);
+
+/* Last error message of this handle ("" if none).  Valid until the next call on it. */
+const char *grace_last_error(const grace_ctx *ctx);
+
+/* Release the handle (not the caller's device memory). NULL is accepted. */
+int grace_destroy(grace_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRACE_H_ */

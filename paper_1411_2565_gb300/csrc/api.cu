@@ -1,0 +1,715 @@
+// C ABI of the LLG hot path: planning, workspace layout, launches and graph replay.
+// The library owns only the host handle; every device byte lives in the caller's
+// workspace (see grace.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fft.cuh"
+#include "grace.h"
+#include "internal.cuh"
+
+using namespace grace;
+
+namespace {
+
+struct FilmHost {
+  int n[3];
+  double cell[3];
+  double Ms, A, Ku, alpha, gamma0;
+  double h[3];
+  int cls;
+};
+
+struct ShapeClass {
+  int n[3];
+  double cell[3];
+  int P[3];
+  int Kx, Ky, Kz, zfft, nslot;
+  size_t t_off;
+};
+
+int pad_len(int n) {
+  int p = 1;
+  while (p < 2 * n - 1) p *= 2;
+  return p;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+constexpr size_t kSmemBudget = 110 * 1024;   // two blocks per SM for the x pass
+constexpr size_t kSmemMax = 200 * 1024;
+constexpr int kThreadsHost = 256;
+constexpr int kTaskCap = 8 * 4 * kThreadsHost;  // points per block the FFT helper can hold
+constexpr int kEnergyBlocks = 304;
+
+}  // namespace
+
+struct grace_ctx {
+  std::vector<FilmHost> films;
+  std::vector<ShapeClass> classes;
+  std::vector<FilmDev> fd;
+  long long ncell = 0;
+  bool fused = true;
+  int TY = 1, RPB = 1, TQ = 1;
+  int units[UK_COUNT] = {0, 0, 0, 0, 0};
+  size_t smem_x = 0, smem_yz = 0, smem_y = 0, smem_z = 0;
+  size_t o_tw = 0, o_films = 0, o_run = 0, o_m0 = 0, o_m1 = 0, o_H = 0, o_part = 0, o_eout = 0;
+  std::vector<size_t> o_S;
+  size_t run_bytes = 0, build_bytes = 0, need = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+  bool bound = false, mset = false;
+  int parity = 0;
+  const float* ms_field = nullptr;
+  const float* h_field = nullptr;
+  bool use_graph = true;
+  int graph_steps = 16;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  float gdt[2] = {0.f, 0.f};
+  std::string err;
+};
+
+namespace {
+
+int fail(grace_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(grace_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, GRACE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GRACE_CUDA(ctx, call)                           \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+bool valid_film(const int n[3], const double cell[3], double Ms, double A, double alpha,
+                double gamma0, std::string& why) {
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < 1 || n[d] > kMaxN) {
+      why = "grid dimension out of range 1..2048";
+      return false;
+    }
+    if (!(cell[d] > 0.0) || !std::isfinite(cell[d])) {
+      why = "cell size must be positive";
+      return false;
+    }
+  }
+  if (!(Ms > 0.0) || !std::isfinite(Ms)) { why = "Ms must be positive"; return false; }
+  if (!(A >= 0.0) || !std::isfinite(A)) { why = "A must be >= 0"; return false; }
+  if (!(alpha >= 0.0) || !std::isfinite(alpha)) { why = "alpha must be >= 0"; return false; }
+  if (!(gamma0 > 0.0) || !std::isfinite(gamma0)) { why = "gamma0 must be positive"; return false; }
+  return true;
+}
+
+// Choose kernels, tile sizes, unit counts and the workspace layout.
+int plan(grace_ctx* c) {
+  // shape classes (films with identical grid and cell share one tensor)
+  for (auto& f : c->films) {
+    int k = -1;
+    for (size_t j = 0; j < c->classes.size(); ++j) {
+      const ShapeClass& s = c->classes[j];
+      if (!std::memcmp(s.n, f.n, sizeof s.n) && !std::memcmp(s.cell, f.cell, sizeof s.cell)) {
+        k = (int)j;
+        break;
+      }
+    }
+    if (k < 0) {
+      ShapeClass s{};
+      std::memcpy(s.n, f.n, sizeof s.n);
+      std::memcpy(s.cell, f.cell, sizeof s.cell);
+      for (int d = 0; d < 3; ++d) s.P[d] = pad_len(f.n[d]);
+      s.Kx = s.P[0] > 1 ? s.P[0] / 2 + 1 : 1;
+      s.Ky = s.P[1] / 2 + 1;
+      s.Kz = s.P[2] / 2 + 1;
+      s.zfft = f.n[2] > 4;
+      s.nslot = s.zfft ? 6 * s.Kz : (f.n[2] == 1 ? 4 : 6 * f.n[2] - 2);
+      c->classes.push_back(s);
+      k = (int)c->classes.size() - 1;
+    }
+    f.cls = k;
+  }
+  // fused y-z pass when every film has nz <= 4 and its slab fits in shared memory
+  c->fused = true;
+  int maxQ = 1, maxnx = 1, maxny = 1, maxPy = 1, maxPz = 1;
+  for (auto& f : c->films) {
+    const ShapeClass& s = c->classes[f.cls];
+    const size_t slab = (size_t)3 * f.n[2] * line_stride(s.P[1]) * sizeof(float2);
+    if (f.n[2] > 4 || slab > kSmemMax || 3 * f.n[2] * s.P[1] > kTaskCap) c->fused = false;
+    maxQ = std::max(maxQ, s.P[0] / 2);
+    maxnx = std::max(maxnx, f.n[0]);
+    maxny = std::max(maxny, f.n[1]);
+    maxPy = std::max(maxPy, s.P[1]);
+    if (s.zfft) maxPz = std::max(maxPz, s.P[2]);
+  }
+  // x pass: TY lines per block
+  int TY = std::min(8, std::max(1, kTaskCap / std::max(1, maxQ)));
+  TY = std::min(TY, maxny);
+  auto smem_x = [&](int ty) {
+    return (size_t)ty * line_stride(maxQ) * sizeof(float2) + (size_t)3 * ty * maxnx * sizeof(float);
+  };
+  while (TY > 1 && smem_x(TY) > kSmemBudget) --TY;
+  c->TY = TY;
+  c->smem_x = smem_x(TY);
+  c->smem_yz = 0;
+  if (c->fused) {
+    for (auto& f : c->films) {
+      const ShapeClass& s = c->classes[f.cls];
+      c->smem_yz = std::max(c->smem_yz, (size_t)3 * f.n[2] * line_stride(s.P[1]) * sizeof(float2));
+    }
+  }
+  int RPB = std::max(1, kTaskCap / maxPy);
+  while (RPB > 1 && (size_t)RPB * line_stride(maxPy) * sizeof(float2) > kSmemBudget) --RPB;
+  c->RPB = RPB;
+  c->smem_y = (size_t)RPB * line_stride(maxPy) * sizeof(float2);
+  int TQ = kThreadsHost;
+  if (maxPz > 1) {
+    TQ = std::max(1, std::min(32, kTaskCap / (3 * maxPz)));
+    while (TQ > 1 && (size_t)3 * TQ * line_stride(maxPz) * sizeof(float2) > kSmemMax) --TQ;
+  }
+  c->TQ = TQ;
+  c->smem_z = maxPz > 1 ? (size_t)3 * TQ * line_stride(maxPz) * sizeof(float2) : 0;
+  if (c->smem_x > kSmemMax || c->smem_y > kSmemMax || c->smem_z > kSmemMax) return GRACE_EUNSUPPORTED;
+
+  // per-film descriptors (pointers filled at bind)
+  c->fd.assign(c->films.size(), FilmDev{});
+  int u[UK_COUNT] = {0, 0, 0, 0, 0};
+  long long cell0 = 0;
+  for (size_t i = 0; i < c->films.size(); ++i) {
+    const FilmHost& h = c->films[i];
+    const ShapeClass& s = c->classes[h.cls];
+    FilmDev& d = c->fd[i];
+    d.nx = h.n[0];
+    d.ny = h.n[1];
+    d.nz = h.n[2];
+    d.ncell = h.n[0] * h.n[1] * h.n[2];
+    d.Px = s.P[0];
+    d.Py = s.P[1];
+    d.Pz = s.P[2];
+    d.Q = s.P[0] > 1 ? s.P[0] / 2 : 0;
+    d.Kx = s.Kx;
+    d.Ky = s.Ky;
+    d.Kz = s.Kz;
+    d.zfft = s.zfft;
+    d.nslot = s.nslot;
+    d.srow = c->fused ? d.ny : d.Py;
+    d.u0[UK_X] = u[UK_X];
+    u[UK_X] += d.nz * ((d.ny + TY - 1) / TY);
+    d.u0[UK_YZ] = u[UK_YZ];
+    u[UK_YZ] += d.Kx;
+    d.u0[UK_Y] = u[UK_Y];
+    u[UK_Y] += (3 * d.nz * d.Kx + RPB - 1) / RPB;
+    d.u0[UK_Z] = u[UK_Z];
+    u[UK_Z] += (d.Kx * d.Py + TQ - 1) / TQ;
+    d.u0[UK_CELL] = 0;
+    d.cell0 = cell0;
+    cell0 += d.ncell;
+    d.idx2 = (float)(1.0 / (h.cell[0] * h.cell[0]));
+    d.idy2 = (float)(1.0 / (h.cell[1] * h.cell[1]));
+    d.idz2 = (float)(1.0 / (h.cell[2] * h.cell[2]));
+    d.Ms = (float)h.Ms;
+    d.cex = (float)(2.0 * h.A / kMu0);
+    d.can = (float)(2.0 * h.Ku / kMu0);
+    d.alpha = (float)h.alpha;
+    d.llg_c = (float)(-h.gamma0 / (1.0 + h.alpha * h.alpha));
+    d.hx = (float)h.h[0];
+    d.hy = (float)h.h[1];
+    d.hz = (float)h.h[2];
+    d.V = h.cell[0] * h.cell[1] * h.cell[2];
+    d.A = h.A;
+    d.Ku = h.Ku;
+  }
+  for (int k = 0; k < UK_COUNT; ++k) c->units[k] = u[k];
+  c->ncell = cell0;
+
+  // workspace layout: [twiddles | descriptors | tensors | runtime (aliased by build scratch)]
+  size_t o = 0;
+  c->o_tw = o;
+  o = al256(o + (size_t)GRACE_LMAX * sizeof(float2));
+  c->o_films = o;
+  o = al256(o + c->films.size() * sizeof(FilmDev));
+  for (auto& s : c->classes) {
+    s.t_off = o;
+    o = al256(o + (size_t)s.Kx * s.nslot * s.Ky * sizeof(float));
+  }
+  c->o_run = o;
+  size_t r = 0;
+  c->o_S.assign(c->films.size(), 0);
+  for (size_t i = 0; i < c->films.size(); ++i) {
+    const FilmDev& d = c->fd[i];
+    c->o_S[i] = r;
+    r = al256(r + (size_t)3 * d.nz * d.Kx * d.srow * sizeof(float2));
+  }
+  const size_t mbytes = al256((size_t)3 * c->ncell * sizeof(float));
+  c->o_m0 = r;
+  r += mbytes;
+  c->o_m1 = r;
+  r += mbytes;
+  c->o_H = r;
+  r += mbytes;
+  c->o_part = r;
+  r = al256(r + (size_t)kEnergyBlocks * 8 * sizeof(double));
+  c->o_eout = r;
+  r = al256(r + 8 * sizeof(double));
+  c->run_bytes = r;
+  size_t b = 0;
+  for (auto& s : c->classes) {
+    const size_t nx = s.n[0], ny = s.n[1], nz = s.n[2];
+    const size_t trig = al256((size_t)2 * (s.P[0] + s.P[1] + s.P[2]) * sizeof(double));
+    const size_t b0 = al256(6 * std::max(nx * ny * nz, nz * s.Ky * s.Kx) * sizeof(double));
+    const size_t b1 = al256(6 * std::max(nz * ny * s.Kx, (size_t)(s.zfft ? s.Kz : 1) * s.Ky * s.Kx) *
+                            sizeof(double));
+    b = std::max(b, trig + b0 + b1);
+  }
+  c->build_bytes = b;
+  c->need = c->o_run + std::max(c->run_bytes, c->build_bytes);
+  return GRACE_OK;
+}
+
+void fill_pointers(grace_ctx* c) {
+  for (size_t i = 0; i < c->films.size(); ++i) {
+    FilmDev& d = c->fd[i];
+    const ShapeClass& s = c->classes[c->films[i].cls];
+    d.m0 = reinterpret_cast<float*>(c->ws + c->o_run + c->o_m0) + 3 * d.cell0;
+    d.m1 = reinterpret_cast<float*>(c->ws + c->o_run + c->o_m1) + 3 * d.cell0;
+    d.S = reinterpret_cast<float2*>(c->ws + c->o_run + c->o_S[i]);
+    d.T = reinterpret_cast<const float*>(c->ws + s.t_off);
+    d.ms_field = c->ms_field ? c->ms_field + d.cell0 : nullptr;
+    d.h_field = c->h_field ? c->h_field + 3 * d.cell0 : nullptr;
+  }
+}
+
+int upload_films(grace_ctx* c) {
+  GRACE_CUDA(c, cudaMemcpyAsync(c->ws + c->o_films, c->fd.data(), c->fd.size() * sizeof(FilmDev),
+                                cudaMemcpyHostToDevice, c->stream));
+  return GRACE_OK;
+}
+
+LaunchP base_lp(const grace_ctx* c) {
+  LaunchP lp{};
+  lp.nfilms = (int)c->films.size();
+  lp.parity = c->parity;
+  lp.dt = 0.f;
+  lp.mask = 15u;
+  lp.out = nullptr;
+  lp.TY = c->TY;
+  lp.RPB = c->RPB;
+  lp.TQ = c->TQ;
+  lp.tw = reinterpret_cast<const float2*>(c->ws + c->o_tw);
+  return lp;
+}
+
+const FilmDev* dfilms(const grace_ctx* c) {
+  return reinterpret_cast<const FilmDev*>(c->ws + c->o_films);
+}
+
+cudaError_t enqueue_conv(const grace_ctx* c, const LaunchP& lp, cudaStream_t s) {
+  const FilmDev* f = dfilms(c);
+  if (c->fused) return launch_yz(f, lp, c->units[UK_YZ], c->smem_yz, s);
+  cudaError_t e = launch_y(-1, f, lp, c->units[UK_Y], c->smem_y, s);
+  if (e != cudaSuccess) return e;
+  e = launch_z(f, lp, c->units[UK_Z], c->smem_z, s);
+  if (e != cudaSuccess) return e;
+  return launch_y(+1, f, lp, c->units[UK_Y], c->smem_y, s);
+}
+
+cudaError_t enqueue_step(const grace_ctx* c, int parity, float dt, cudaStream_t s) {
+  LaunchP lp = base_lp(c);
+  lp.parity = parity;
+  lp.dt = dt;
+  cudaError_t e = enqueue_conv(c, lp, s);
+  if (e != cudaSuccess) return e;
+  return launch_xpass(XM_STEP, dfilms(c), lp, c->units[UK_X], c->smem_x, s);
+}
+
+int enqueue_heff(grace_ctx* c, float* out, unsigned mask) {
+  LaunchP lp = base_lp(c);
+  lp.mask = mask;
+  lp.out = out;
+  if (mask & GRACE_TERM_DEMAG) {
+    cudaError_t e = enqueue_conv(c, lp, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "demag convolution launch");
+  }
+  cudaError_t e = launch_xpass(XM_HEFF, dfilms(c), lp, c->units[UK_X], c->smem_x, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "x pass launch");
+  return GRACE_OK;
+}
+
+void drop_graphs(grace_ctx* c) {
+  for (int p = 0; p < 2; ++p) {
+    if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
+    c->gexec[p] = nullptr;
+  }
+}
+
+int ready(grace_ctx* c, bool need_m) {
+  if (!c) return GRACE_EINVAL;
+  if (!c->bound) return fail(c, GRACE_ESTATE, "grace_bind has not been called");
+  if (need_m && !c->mset) return fail(c, GRACE_ESTATE, "grace_set_m has not been called");
+  return GRACE_OK;
+}
+
+}  // namespace
+
+// Kernel attribute setup lives with the kernels; declared here.
+namespace grace {
+cudaError_t configure_kernels(size_t smem_x, size_t smem_yz, size_t smem_y, size_t smem_z);
+}
+
+extern "C" {
+
+int grace_create(grace_ctx** out, const int grid[3], const double cell_m[3], double Ms, double A,
+                 double Ku, double alpha, double gamma0) {
+  if (!out) return GRACE_EINVAL;
+  *out = nullptr;
+  if (!grid || !cell_m) return GRACE_EINVAL;
+  return grace_batch_create(out, 1, grid, cell_m, &Ms, &A, &Ku, &alpha, &gamma0);
+}
+
+int grace_batch_create(grace_ctx** out, int nfilms, const int* grid, const double* cell_m,
+                       const double* Ms, const double* A, const double* Ku, const double* alpha,
+                       const double* gamma0) {
+  if (!out) return GRACE_EINVAL;
+  *out = nullptr;
+  if (nfilms < 1 || nfilms > 65536 || !grid || !cell_m || !Ms || !A || !Ku || !alpha || !gamma0)
+    return GRACE_EINVAL;
+  grace_ctx* c = new (std::nothrow) grace_ctx();
+  if (!c) return GRACE_EINVAL;
+  for (int i = 0; i < nfilms; ++i) {
+    FilmHost f{};
+    for (int d = 0; d < 3; ++d) {
+      f.n[d] = grid[3 * i + d];
+      f.cell[d] = cell_m[3 * i + d];
+    }
+    f.Ms = Ms[i];
+    f.A = A[i];
+    f.Ku = Ku[i];
+    f.alpha = alpha[i];
+    f.gamma0 = gamma0[i];
+    std::string why;
+    if (!valid_film(f.n, f.cell, f.Ms, f.A, f.alpha, f.gamma0, why) || !std::isfinite(f.Ku)) {
+      delete c;
+      return GRACE_EINVAL;
+    }
+    c->films.push_back(f);
+  }
+  int st = plan(c);
+  if (st != GRACE_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return GRACE_OK;
+}
+
+int grace_workspace_size(const grace_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return GRACE_EINVAL;
+  *bytes = c->need;
+  return GRACE_OK;
+}
+
+int grace_ncells(const grace_ctx* c, long long* n) {
+  if (!c || !n) return GRACE_EINVAL;
+  *n = c->ncell;
+  return GRACE_OK;
+}
+
+int grace_bind(grace_ctx* c, void* dev_ws, size_t bytes, void* cuda_stream) {
+  if (!c) return GRACE_EINVAL;
+  if (!dev_ws) return fail(c, GRACE_EINVAL, "workspace pointer is NULL");
+  if ((reinterpret_cast<uintptr_t>(dev_ws) & 255u) != 0)
+    return fail(c, GRACE_EWORKSPACE, "workspace must be 256-byte aligned");
+  if (bytes < c->need) return fail(c, GRACE_EWORKSPACE, "workspace smaller than grace_workspace_size");
+  drop_graphs(c);
+  c->ws = static_cast<char*>(dev_ws);
+  c->ws_bytes = bytes;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->bound = false;
+  c->mset = false;
+  c->parity = 0;
+  GRACE_CUDA(c, configure_kernels(c->smem_x, c->smem_yz, c->smem_y, c->smem_z));
+  // twiddle table exp(-2 pi i m / LMAX), FP64 on the host, rounded to FP32
+  std::vector<float2> tw(GRACE_LMAX);
+  for (int m = 0; m < GRACE_LMAX; ++m) {
+    const double a = 2.0 * M_PI * (double)m / GRACE_LMAX;
+    tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  GRACE_CUDA(c, cudaMemcpyAsync(c->ws + c->o_tw, tw.data(), tw.size() * sizeof(float2),
+                                cudaMemcpyHostToDevice, c->stream));
+  // demag tensors, one per shape class, built in the (aliased) runtime region
+  std::vector<std::vector<double>> trig_host(c->classes.size());
+  for (size_t k = 0; k < c->classes.size(); ++k) {
+    const ShapeClass& s = c->classes[k];
+    std::vector<double>& tr = trig_host[k];
+    tr.resize((size_t)2 * (s.P[0] + s.P[1] + s.P[2]));
+    size_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int P = s.P[d];
+      for (int m = 0; m < P; ++m) {
+        const double a = 2.0 * M_PI * (double)m / (double)P;
+        tr[off + m] = std::cos(a);
+        tr[off + P + m] = std::sin(a);
+      }
+      off += 2 * P;
+    }
+    char* base = c->ws + c->o_run;
+    const size_t nx = s.n[0], ny = s.n[1], nz = s.n[2];
+    const size_t trig_b = al256(tr.size() * sizeof(double));
+    const size_t b0 = al256(6 * std::max(nx * ny * nz, nz * s.Ky * s.Kx) * sizeof(double));
+    GRACE_CUDA(c, cudaMemcpyAsync(base, tr.data(), tr.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->stream));
+    TensorJob j{};
+    j.nx = s.n[0];
+    j.ny = s.n[1];
+    j.nz = s.n[2];
+    j.Px = s.P[0];
+    j.Py = s.P[1];
+    j.Pz = s.P[2];
+    j.Kx = s.Kx;
+    j.Ky = s.Ky;
+    j.Kz = s.Kz;
+    j.zfft = s.zfft;
+    j.nslot = s.nslot;
+    j.dx = s.cell[0];
+    j.dy = s.cell[1];
+    j.dz = s.cell[2];
+    j.trig_x = reinterpret_cast<const double*>(base);
+    j.trig_y = j.trig_x + 2 * s.P[0];
+    j.trig_z = j.trig_y + 2 * s.P[1];
+    j.buf0 = reinterpret_cast<double*>(base + trig_b);
+    j.buf1 = reinterpret_cast<double*>(base + trig_b + b0);
+    j.T = reinterpret_cast<float*>(c->ws + s.t_off);
+    GRACE_CUDA(c, launch_tensor_build(j, c->stream));
+    // the next class reuses the scratch: order on the stream is enough
+  }
+  fill_pointers(c);
+  int st = upload_films(c);
+  if (st != GRACE_OK) return st;
+  GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->use_graph && !c->cap) GRACE_CUDA(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  c->bound = true;
+  return GRACE_OK;
+}
+
+int grace_set_m(grace_ctx* c, const float* dev_m) {
+  int st = ready(c, false);
+  if (st) return st;
+  if (!dev_m) return fail(c, GRACE_EINVAL, "m pointer is NULL");
+  float* dst = reinterpret_cast<float*>(c->ws + c->o_run + (c->parity ? c->o_m1 : c->o_m0));
+  GRACE_CUDA(c, cudaMemcpyAsync(dst, dev_m, (size_t)3 * c->ncell * sizeof(float),
+                                cudaMemcpyDeviceToDevice, c->stream));
+  LaunchP lp = base_lp(c);
+  GRACE_CUDA(c, launch_xpass(XM_R2C, dfilms(c), lp, c->units[UK_X], c->smem_x, c->stream));
+  c->mset = true;
+  return GRACE_OK;
+}
+
+int grace_set_m_host(grace_ctx* c, const float* host_m) {
+  int st = ready(c, false);
+  if (st) return st;
+  if (!host_m) return fail(c, GRACE_EINVAL, "m pointer is NULL");
+  float* dst = reinterpret_cast<float*>(c->ws + c->o_run + (c->parity ? c->o_m1 : c->o_m0));
+  GRACE_CUDA(c, cudaMemcpyAsync(dst, host_m, (size_t)3 * c->ncell * sizeof(float),
+                                cudaMemcpyHostToDevice, c->stream));
+  LaunchP lp = base_lp(c);
+  GRACE_CUDA(c, launch_xpass(XM_R2C, dfilms(c), lp, c->units[UK_X], c->smem_x, c->stream));
+  c->mset = true;
+  return GRACE_OK;
+}
+
+int grace_get_m(const grace_ctx* cc, float* dev_m) {
+  grace_ctx* c = const_cast<grace_ctx*>(cc);
+  int st = ready(c, true);
+  if (st) return st;
+  if (!dev_m) return fail(c, GRACE_EINVAL, "m pointer is NULL");
+  const float* src = reinterpret_cast<const float*>(c->ws + c->o_run + (c->parity ? c->o_m1 : c->o_m0));
+  GRACE_CUDA(c, cudaMemcpyAsync(dev_m, src, (size_t)3 * c->ncell * sizeof(float),
+                                cudaMemcpyDeviceToDevice, c->stream));
+  return GRACE_OK;
+}
+
+int grace_get_m_host(grace_ctx* c, float* host_m) {
+  int st = ready(c, true);
+  if (st) return st;
+  if (!host_m) return fail(c, GRACE_EINVAL, "m pointer is NULL");
+  const float* src = reinterpret_cast<const float*>(c->ws + c->o_run + (c->parity ? c->o_m1 : c->o_m0));
+  GRACE_CUDA(c, cudaMemcpyAsync(host_m, src, (size_t)3 * c->ncell * sizeof(float),
+                                cudaMemcpyDeviceToHost, c->stream));
+  GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
+  return GRACE_OK;
+}
+
+int grace_set_hext(grace_ctx* c, const double h[3]) {
+  if (!c || !h) return GRACE_EINVAL;
+  for (size_t i = 0; i < c->films.size(); ++i) {
+    int st = grace_set_film_hext(c, (int)i, h);
+    if (st) return st;
+  }
+  return GRACE_OK;
+}
+
+int grace_set_film_hext(grace_ctx* c, int film, const double h[3]) {
+  if (!c || !h) return GRACE_EINVAL;
+  if (film < 0 || film >= (int)c->films.size()) return fail(c, GRACE_EINVAL, "film index out of range");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(h[d])) return fail(c, GRACE_EINVAL, "field must be finite");
+  FilmHost& f = c->films[film];
+  for (int d = 0; d < 3; ++d) f.h[d] = h[d];
+  c->fd[film].hx = (float)h[0];
+  c->fd[film].hy = (float)h[1];
+  c->fd[film].hz = (float)h[2];
+  if (c->bound) return upload_films(c);
+  return GRACE_OK;
+}
+
+int grace_set_hext_field(grace_ctx* c, const float* dev_h) {
+  int st = ready(c, false);
+  if (st) return st;
+  c->h_field = dev_h;
+  fill_pointers(c);
+  return upload_films(c);
+}
+
+int grace_set_ms_field(grace_ctx* c, const float* dev_ms) {
+  int st = ready(c, false);
+  if (st) return st;
+  c->ms_field = dev_ms;
+  fill_pointers(c);
+  st = upload_films(c);
+  if (st) return st;
+  if (c->mset) {   // the spectrum holds FFT(Ms m): refresh it
+    LaunchP lp = base_lp(c);
+    GRACE_CUDA(c, launch_xpass(XM_R2C, dfilms(c), lp, c->units[UK_X], c->smem_x, c->stream));
+  }
+  return GRACE_OK;
+}
+
+int grace_heff(grace_ctx* c, float* dev_h, unsigned mask) {
+  int st = ready(c, true);
+  if (st) return st;
+  if (!dev_h) return fail(c, GRACE_EINVAL, "output pointer is NULL");
+  if (mask & ~15u) return fail(c, GRACE_EINVAL, "unknown term bits");
+  return enqueue_heff(c, dev_h, mask);
+}
+
+int grace_step(grace_ctx* c, int n, double dt) {
+  int st = ready(c, true);
+  if (st) return st;
+  if (n < 0) return fail(c, GRACE_EINVAL, "n must be >= 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GRACE_EINVAL, "dt must be positive");
+  const float fdt = (float)dt;
+  int done = 0;
+  const int G = c->graph_steps;
+  if (c->use_graph && c->cap && n >= G) {
+    const int p = c->parity;
+    if (!c->gexec[p] || c->gdt[p] != fdt) {
+      if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
+      c->gexec[p] = nullptr;
+      cudaGraph_t g = nullptr;
+      GRACE_CUDA(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int s = 0; s < G && e == cudaSuccess; ++s) e = enqueue_step(c, (p + s) & 1, fdt, c->cap);
+      cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e, "graph capture");
+      }
+      if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&c->gexec[p], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+      c->gdt[p] = fdt;
+    }
+    while (n - done >= G) {
+      GRACE_CUDA(c, cudaGraphLaunch(c->gexec[p], c->stream));
+      done += G;
+    }
+  }
+  for (; done < n; ++done) {
+    GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, c->stream));
+    c->parity ^= 1;
+  }
+  return GRACE_OK;
+}
+
+int grace_energy(grace_ctx* c, double out[5], double mavg[3]) {
+  int st = ready(c, true);
+  if (st) return st;
+  float* H = reinterpret_cast<float*>(c->ws + c->o_run + c->o_H);
+  st = enqueue_heff(c, H, GRACE_TERM_DEMAG);
+  if (st) return st;
+  LaunchP lp = base_lp(c);
+  double* part = reinterpret_cast<double*>(c->ws + c->o_run + c->o_part);
+  double* res = reinterpret_cast<double*>(c->ws + c->o_run + c->o_eout);
+  GRACE_CUDA(c, launch_energy(dfilms(c), lp, H, c->ncell, part, kEnergyBlocks, res, c->stream));
+  double h[8];
+  GRACE_CUDA(c, cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (out) {
+    for (int k = 0; k < 4; ++k) out[k] = h[k];
+    out[4] = h[0] + h[1] + h[2] + h[3];
+  }
+  if (mavg)
+    for (int k = 0; k < 3; ++k) mavg[k] = h[4 + k] / (double)c->ncell;
+  if (h[7] != 0.0 || !std::isfinite(h[4] + h[5] + h[6]))
+    return fail(c, GRACE_ENONFINITE, "non-finite magnetisation");
+  return GRACE_OK;
+}
+
+int grace_backward_workspace_size(const grace_ctx* c, int n, int ckpt_every, size_t* bytes) {
+  if (!c || !bytes || n < 0 || ckpt_every < 1) return GRACE_EINVAL;
+  *bytes = 0;
+  return fail(const_cast<grace_ctx*>(c), GRACE_EUNSUPPORTED, "backward not built");
+}
+
+int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt_every, void* scratch,
+                   size_t scratch_bytes, float* dL_dhext, float* dL_dms, float* dL_dm0) {
+  (void)dL_dmT; (void)n; (void)dt; (void)ckpt_every; (void)scratch; (void)scratch_bytes;
+  (void)dL_dhext; (void)dL_dms; (void)dL_dm0;
+  if (!c) return GRACE_EINVAL;
+  return fail(c, GRACE_EUNSUPPORTED, "backward not built");
+}
+
+int grace_set_option(grace_ctx* c, int option, long long value) {
+  if (!c) return GRACE_EINVAL;
+  switch (option) {
+    case GRACE_OPT_GRAPH:
+      if (value != 0 && value != 1) return fail(c, GRACE_EINVAL, "GRACE_OPT_GRAPH takes 0 or 1");
+      c->use_graph = value != 0;
+      drop_graphs(c);
+      if (c->use_graph && c->bound && !c->cap)
+        GRACE_CUDA(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+      return GRACE_OK;
+    case GRACE_OPT_GRAPH_STEPS:
+      if (value < 2 || value > 4096 || (value & 1)) return fail(c, GRACE_EINVAL, "graph steps: even, 2..4096");
+      c->graph_steps = (int)value;
+      drop_graphs(c);
+      return GRACE_OK;
+    default:
+      return fail(c, GRACE_EINVAL, "unknown option");
+  }
+}
+
+const char* grace_last_error(const grace_ctx* c) { return c ? c->err.c_str() : "null handle"; }
+
+int grace_destroy(grace_ctx* c) {
+  if (!c) return GRACE_OK;
+  drop_graphs(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+  return GRACE_OK;
+}
+
+}  // extern "C"

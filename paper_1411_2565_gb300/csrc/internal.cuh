@@ -1,0 +1,104 @@
+// Internal device-side data structures shared by the kernels and the host planner.
+//
+// HBM layout of one film (all FP32; the caller's workspace holds every buffer):
+//   m[2]  : double-buffered unit magnetisation [3][nz][ny][nx]
+//   S     : x-transformed magnetisation / field spectrum [3][nz][Kx][srow] complex,
+//           y contiguous.  Between steps S holds FFT_x(Ms m_n) for the n_y real rows;
+//           the y (and z) passes work on it in place.
+//   T     : demag tensor spectrum [Kx][nslot][Ky] real, shared by films of one shape,
+//           pre-multiplied by -1/(Px Py [Pz]) so that H^ = T . M^.
+//     direct-z mode (nz <= 4): slots 4*dz + {xx, yy, zz, xy} for dz = 0..nz-1, then
+//       4*nz + 2*(dz-1) + {xz, yz} for dz = 1..nz-1; the xz / yz entries are the
+//       imaginary parts of the (x,y)-transformed tensor at z offset dz.
+//     FFT-z mode: slot comp*Kz + kz for comp in {xx, yy, zz, xy, xz, yz}, kz = 0..Pz/2.
+//     Components odd in y (xy, yz) change sign for ky > Py/2, odd in z (xz, yz) for
+//     kz > Pz/2 or dz < 0.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace grace {
+
+constexpr double kMu0 = 1.2566370614359172954e-6;   // 4 pi 1e-7
+constexpr int kNewellRadius = 24;                    // Chebyshev radius of the Newell region (cells)
+constexpr int kMaxN = 2048;                          // per-axis cell limit (P <= GRACE_LMAX)
+
+enum UnitKind { UK_X = 0, UK_YZ = 1, UK_Y = 2, UK_Z = 3, UK_CELL = 4, UK_COUNT = 5 };
+
+struct FilmDev {
+  int nx, ny, nz, ncell;
+  int Px, Py, Pz;
+  int Q;        // Px/2 complex points of the x transform (0 when Px == 1)
+  int Kx;       // Q + 1 stored kx columns (1 when Px == 1)
+  int Ky;       // Py/2 + 1 stored ky rows of the tensor
+  int Kz;       // Pz/2 + 1 (FFT-z mode)
+  int zfft;     // 1: FFT along z; 0: direct convolution along z
+  int nslot;    // tensor slots per (kx, ky)
+  int srow;     // row stride of S along y (ny when fused, Py when split)
+  int u0[UK_COUNT];   // first work unit of this film per unit kind
+  long long cell0;    // first cell of this film in concatenated arrays
+  float idx2, idy2, idz2;  // 1/dx^2, 1/dy^2, 1/dz^2
+  float Ms;                // uniform Ms (A/m)
+  float cex;               // 2A/mu0
+  float can;               // 2Ku/mu0
+  float alpha;
+  float llg_c;             // -gamma0/(1+alpha^2)
+  float hx, hy, hz;        // uniform H_ext (A/m)
+  double V, A, Ku;         // cell volume and raw constants for the FP64 energies
+  float* m0;
+  float* m1;
+  float2* S;
+  const float* T;
+  const float* ms_field;   // per-cell Ms of this film or nullptr
+  const float* h_field;    // per-cell H_ext of this film or nullptr
+};
+
+enum XMode { XM_R2C = 0, XM_HEFF = 1, XM_STEP = 2 };
+
+struct LaunchP {
+  int nfilms;
+  int parity;       // m buffer holding the current state
+  float dt;
+  unsigned mask;    // term bits (XM_HEFF)
+  float* out;       // H output (XM_HEFF), concatenated films
+  int TY;           // y lines per x-pass block
+  int RPB;          // rows per block in the split y pass
+  int TQ;           // columns per block in the split z pass
+  const float2* tw; // twiddle table, GRACE_LMAX entries
+};
+
+// Film owning work unit `unit` of kind `kind` (films sorted by u0[kind]).
+__device__ __forceinline__ int find_film(const FilmDev* __restrict__ films, int nfilms, int kind,
+                                         int unit) {
+  int lo = 0, hi = nfilms - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (films[mid].u0[kind] <= unit) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Host-side launchers (hotpath.cu, tensor.cu).
+cudaError_t launch_xpass(int mode, const FilmDev* films, const LaunchP& lp, int nunits, size_t smem,
+                         cudaStream_t s);
+cudaError_t launch_yz(const FilmDev* films, const LaunchP& lp, int nunits, size_t smem, cudaStream_t s);
+cudaError_t launch_y(int dir, const FilmDev* films, const LaunchP& lp, int nunits, size_t smem,
+                     cudaStream_t s);
+cudaError_t launch_z(const FilmDev* films, const LaunchP& lp, int nunits, size_t smem, cudaStream_t s);
+cudaError_t launch_energy(const FilmDev* films, const LaunchP& lp, const float* hdemag,
+                          long long ntotal, double* partial, int nblocks, double* result,
+                          cudaStream_t s);
+
+struct TensorJob {
+  int nx, ny, nz, Px, Py, Pz, Kx, Ky, Kz, zfft, nslot;
+  double dx, dy, dz;
+  double* buf0;
+  double* buf1;
+  const double* trig_x;   // [cos(2 pi m/Px), sin(...)] m < Px, 2*Px doubles
+  const double* trig_y;
+  const double* trig_z;
+  float* T;
+};
+cudaError_t launch_tensor_build(const TensorJob& job, cudaStream_t s);
+
+}  // namespace grace

@@ -1,0 +1,163 @@
+"""Python binding of the C ABI: ``Grace`` (one film) and ``GraceBatch`` (an ensemble).
+
+PyTorch supplies device memory (the workspace and I/O tensors) and the CUDA stream;
+every step of the computation runs in libgrace.so.  Field tensors are FP32
+``[3, nz, ny, nx]`` per film (a batch uses one flat tensor: films concatenated).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import TERM_ALL, check, dvec, ivec
+
+GAMMA0 = 2.211e5
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor, numel: int, what: str) -> int:
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{what}: need a contiguous float32 CUDA tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{what}: expected {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class _Base:
+    def _init(self, ctx: C.c_void_p, device, stream):
+        self._L = _lib.load()
+        self.ctx = ctx
+        self.device = torch.device(device)
+        n = C.c_longlong()
+        check(self._L.grace_ncells(ctx, C.byref(n)), "grace_ncells", ctx)
+        self.ncell = int(n.value)
+        sz = C.c_size_t()
+        check(self._L.grace_workspace_size(ctx, C.byref(sz)), "grace_workspace_size", ctx)
+        self.workspace_bytes = int(sz.value)
+        self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8,
+                                     device=self.device)
+        self.stream = stream
+        check(self._L.grace_bind(ctx, self.workspace.data_ptr(), self.workspace_bytes,
+                                 _stream_ptr(stream)), "grace_bind", ctx)
+        self._keep = {}
+
+    # -- state ------------------------------------------------------------------
+    def set_m(self, m: torch.Tensor):
+        check(self._L.grace_set_m(self.ctx, _dev_ptr(m, 3 * self.ncell, "m")), "grace_set_m", self.ctx)
+
+    def get_m(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(3 * self.ncell, dtype=torch.float32, device=self.device)
+        check(self._L.grace_get_m(self.ctx, _dev_ptr(out, 3 * self.ncell, "out")), "grace_get_m",
+              self.ctx)
+        return out
+
+    def set_m_host(self, m: np.ndarray):
+        a = np.ascontiguousarray(m, dtype=np.float32)
+        if a.size != 3 * self.ncell:
+            raise ValueError("m: wrong size")
+        check(self._L.grace_set_m_host(self.ctx, a.ctypes.data), "grace_set_m_host", self.ctx)
+        self._keep["m_host"] = a   # the copy is queued; keep the buffer alive
+
+    def get_m_host(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(3 * self.ncell, dtype=np.float32)
+        check(self._L.grace_get_m_host(self.ctx, out.ctypes.data), "grace_get_m_host", self.ctx)
+        return out
+
+    # -- parameters ---------------------------------------------------------------
+    def set_hext(self, h: Sequence[float]):
+        check(self._L.grace_set_hext(self.ctx, dvec(h)), "grace_set_hext", self.ctx)
+
+    def set_hext_field(self, h: Optional[torch.Tensor]):
+        ptr = None if h is None else _dev_ptr(h, 3 * self.ncell, "hext field")
+        check(self._L.grace_set_hext_field(self.ctx, ptr), "grace_set_hext_field", self.ctx)
+        self._keep["h"] = h
+
+    def set_ms_field(self, ms: Optional[torch.Tensor]):
+        ptr = None if ms is None else _dev_ptr(ms, self.ncell, "Ms field")
+        check(self._L.grace_set_ms_field(self.ctx, ptr), "grace_set_ms_field", self.ctx)
+        self._keep["ms"] = ms
+
+    def set_option(self, option: int, value: int):
+        check(self._L.grace_set_option(self.ctx, option, value), "grace_set_option", self.ctx)
+
+    # -- compute ------------------------------------------------------------------
+    def heff(self, mask: int = TERM_ALL, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(3 * self.ncell, dtype=torch.float32, device=self.device)
+        check(self._L.grace_heff(self.ctx, _dev_ptr(out, 3 * self.ncell, "out"), mask), "grace_heff",
+              self.ctx)
+        return out
+
+    def step(self, n: int, dt: float):
+        check(self._L.grace_step(self.ctx, int(n), float(dt)), "grace_step", self.ctx)
+
+    def energy(self):
+        e = (C.c_double * 5)()
+        mv = (C.c_double * 3)()
+        check(self._L.grace_energy(self.ctx, e, mv), "grace_energy", self.ctx)
+        names = ("exch", "anis", "demag", "zeeman", "total")
+        return dict(zip(names, list(e))), np.array(list(mv))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._L.grace_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Grace(_Base):
+    """One rectangular film (grid (nx, ny, nz), cell (dx, dy, dz) in metres)."""
+
+    def __init__(self, grid, cell, Ms, A, Ku=0.0, alpha=0.1, gamma0=GAMMA0, device="cuda",
+                 stream: Optional[torch.cuda.Stream] = None):
+        L = _lib.load()
+        ctx = C.c_void_p()
+        check(L.grace_create(C.byref(ctx), ivec(grid), dvec(cell), float(Ms), float(A), float(Ku),
+                             float(alpha), float(gamma0)), "grace_create")
+        self.grid = tuple(int(g) for g in grid)
+        self._init(ctx, device, stream)
+
+    @property
+    def shape(self):
+        nx, ny, nz = self.grid
+        return (3, nz, ny, nx)
+
+
+class GraceBatch(_Base):
+    """Independent films stepped together; arrays are the films concatenated in order."""
+
+    def __init__(self, films, device="cuda", stream: Optional[torch.cuda.Stream] = None):
+        L = _lib.load()
+        ctx = C.c_void_p()
+        n = len(films)
+        grid = [g for f in films for g in f.grid]
+        cell = [c for f in films for c in f.cell]
+        check(L.grace_batch_create(C.byref(ctx), n, ivec(grid), dvec(cell),
+                                   dvec([f.Ms for f in films]), dvec([f.A for f in films]),
+                                   dvec([f.Ku for f in films]), dvec([f.alpha for f in films]),
+                                   dvec([f.gamma0 for f in films])), "grace_batch_create")
+        self.films = list(films)
+        self._init(ctx, device, stream)
+        for i, f in enumerate(films):
+            check(L.grace_set_film_hext(ctx, i, dvec(f.hext)), "grace_set_film_hext", ctx)
+        self.offsets = np.cumsum([0] + [3 * f.ncells for f in films])
+
+    def split(self, flat: torch.Tensor):
+        """Per-film views [3, nz, ny, nx] of a concatenated field."""
+        return [flat[self.offsets[i]:self.offsets[i + 1]].view(3, f.grid[2], f.grid[1], f.grid[0])
+                for i, f in enumerate(self.films)]

@@ -1,0 +1,106 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point that
+include/grace.h declares, and validates arguments and call order on the host."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1411_2565_gb300 import _lib
+from paper_1411_2565_gb300 import build as libbuild
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "grace.h")
+EINVAL, EWORKSPACE, ESTATE = -1, -2, -5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*)\s*(grace_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.SIGNATURES)
+
+
+def _create(lib, grid=(16, 8, 2), cell=(3e-9, 3e-9, 3e-9), Ms=8e5, A=1.3e-11, Ku=0.0, alpha=0.1,
+            g0=2.211e5):
+    ctx = C.c_void_p()
+    st = lib.grace_create(C.byref(ctx), _lib.ivec(grid), _lib.dvec(cell), Ms, A, Ku, alpha, g0)
+    return st, ctx
+
+
+@pytest.mark.parametrize("kw", [dict(grid=(0, 8, 2)), dict(grid=(16, 8, 4097)), dict(cell=(0, 1e-9, 1e-9)),
+                                dict(Ms=0.0), dict(Ms=-1.0), dict(A=-1e-11), dict(alpha=-0.1),
+                                dict(g0=0.0), dict(Ms=float("nan"))])
+def test_create_rejects_invalid_arguments(lib, kw):
+    st, ctx = _create(lib, **kw)
+    assert st == EINVAL
+    assert not ctx.value
+
+
+def test_create_plans_workspace_and_counts_cells(lib):
+    st, ctx = _create(lib, grid=(1024, 256, 4), cell=(2e-9,) * 3)
+    assert st == 0
+    n = C.c_longlong()
+    assert lib.grace_ncells(ctx, C.byref(n)) == 0 and n.value == 1024 * 256 * 4
+    sz = C.c_size_t()
+    assert lib.grace_workspace_size(ctx, C.byref(sz)) == 0
+    N = n.value
+    Kx, Ky = 1025, 257
+    tensor = Kx * (6 * 4 - 2) * Ky * 4
+    spectrum = 3 * 4 * Kx * 256 * 8
+    state = 3 * (3 * N * 4)
+    assert sz.value >= tensor + spectrum + state
+    assert sz.value < 2 * (tensor + spectrum + state) + (1 << 20)
+    lib.grace_destroy(ctx)
+
+
+def test_call_order_and_workspace_checks(lib):
+    st, ctx = _create(lib)
+    assert st == 0
+    out = C.c_void_p(0x1000)
+    assert lib.grace_step(ctx, 1, 1e-14) == ESTATE
+    assert lib.grace_heff(ctx, out, 15) == ESTATE
+    assert lib.grace_set_m(ctx, out) == ESTATE
+    assert b"bind" in lib.grace_last_error(ctx)
+    sz = C.c_size_t()
+    lib.grace_workspace_size(ctx, C.byref(sz))
+    assert lib.grace_bind(ctx, None, sz.value, None) == EINVAL
+    assert lib.grace_bind(ctx, C.c_void_p(0x10010), sz.value, None) == EWORKSPACE
+    assert lib.grace_bind(ctx, C.c_void_p(0x10000), sz.value - 1, None) == EWORKSPACE
+    assert lib.grace_set_option(ctx, 99, 1) == EINVAL
+    assert lib.grace_set_option(ctx, _lib.OPT_GRAPH_STEPS, 3) == EINVAL
+    assert lib.grace_set_option(ctx, _lib.OPT_GRAPH_STEPS, 8) == 0
+    assert lib.grace_set_film_hext(ctx, 1, _lib.dvec([0, 0, 0])) == EINVAL
+    assert lib.grace_set_hext(ctx, _lib.dvec([1.0, 2.0, 3.0])) == 0
+    assert lib.grace_destroy(ctx) == 0
+    assert lib.grace_destroy(None) == 0
+
+
+def test_batch_create_shares_tensor_per_shape(lib):
+    grids = [(64, 16, 1), (128, 32, 1), (64, 16, 1), (200, 50, 1)]
+    n = len(grids)
+    ctx = C.c_void_p()
+    st = lib.grace_batch_create(C.byref(ctx), n, _lib.ivec([g for t in grids for g in t]),
+                                _lib.dvec([3e-9] * 3 * n), _lib.dvec([8e5] * n),
+                                _lib.dvec([1.3e-11] * n), _lib.dvec([0.0] * n),
+                                _lib.dvec([0.1] * n), _lib.dvec([2.211e5] * n))
+    assert st == 0
+    cnt = C.c_longlong()
+    lib.grace_ncells(ctx, C.byref(cnt))
+    assert cnt.value == sum(a * b * c for a, b, c in grids)
+    lib.grace_destroy(ctx)
+    bad = C.c_void_p()
+    assert lib.grace_batch_create(C.byref(bad), 0, None, None, None, None, None, None, None) == EINVAL
