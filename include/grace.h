@@ -62,7 +62,19 @@ enum {
 /* Options for grace_set_option. */
 enum {
   GRACE_OPT_GRAPH = 1,        /* 1 (default): grace_step replays captured CUDA graphs; 0: plain launches */
-  GRACE_OPT_GRAPH_STEPS = 2   /* steps per captured graph (even, >= 2; default 16) */
+  GRACE_OPT_GRAPH_STEPS = 2,  /* steps per captured graph (even, >= 2; default 16) */
+  GRACE_OPT_TILE_X = 3,       /* y lines per x-pass block (0 = automatic); before grace_bind only */
+  GRACE_OPT_TILE_YZ = 4       /* kx columns per fused y-z block (0 = automatic); before grace_bind only */
+};
+
+/* Kernel kinds reported by grace_trace_read. */
+enum {
+  GRACE_KERNEL_YZ_FAST = 0,   /* fused y FFT + tensor product + inverse y, compile-time length */
+  GRACE_KERNEL_X_FAST = 1,    /* fused x C2R + H_eff + Euler + x R2C, compile-time length */
+  GRACE_KERNEL_YZ = 2,        /* the same two passes with runtime lengths (small or mixed films) */
+  GRACE_KERNEL_Y = 3,         /* split path for thick films: y FFT (both directions) */
+  GRACE_KERNEL_Z = 4,         /* split path: z FFT + tensor product + inverse z */
+  GRACE_KERNEL_X = 5          /* runtime-length x pass */
 };
 
 /*
@@ -152,6 +164,16 @@ int grace_backward_workspace_size(const grace_ctx *ctx, int n, int ckpt_every, s
 int grace_backward(grace_ctx *ctx, const float *dev_dL_dmT, int n, double dt_s, int ckpt_every,
                    void *dev_scratch, size_t scratch_bytes, float *dev_dL_dhext,
                    float *dev_dL_dms, float *dev_dL_dm0);
+
+/*
+ * grace_trace - when on (1), every kernel launched by grace_step / grace_heff /
+ * grace_set_m is bracketed by CUDA events on the bound stream (grace_step then uses plain
+ * launches instead of graphs).  grace_trace_read synchronises on the last event and
+ * returns, per GRACE_KERNEL_* kind, the summed device time in ms and the launch count
+ * since the previous read (8 entries each); it then resets them.
+ */
+int grace_trace(grace_ctx *ctx, int on);
+int grace_trace_read(grace_ctx *ctx, double ms[8], long long counts[8]);
 
 /* grace_set_option - see GRACE_OPT_*. */
 int grace_set_option(grace_ctx *ctx, int option, long long value);

@@ -12,7 +12,8 @@ STATUS = {0: "GRACE_OK", -1: "GRACE_EINVAL", -2: "GRACE_EWORKSPACE", -3: "GRACE_
           -4: "GRACE_ETIMEOUT", -5: "GRACE_ESTATE", -6: "GRACE_ENONFINITE",
           -7: "GRACE_EUNSUPPORTED"}
 TERM_DEMAG, TERM_EXCH, TERM_ANIS, TERM_ZEEMAN, TERM_ALL = 1, 2, 4, 8, 15
-OPT_GRAPH, OPT_GRAPH_STEPS = 1, 2
+OPT_GRAPH, OPT_GRAPH_STEPS, OPT_TILE_X, OPT_TILE_YZ = 1, 2, 3, 4
+KERNEL_NAMES = ("yz_fast", "x_fast", "yz", "y", "z", "x")
 
 _P = C.c_void_p
 _I = C.c_int
@@ -41,6 +42,8 @@ SIGNATURES = {
     "grace_backward_workspace_size": (_I, [_P, _I, _I, C.POINTER(_SZ)]),
     "grace_backward": (_I, [_P, _P, _I, _D, _I, _P, _SZ, _P, _P, _P]),
     "grace_set_option": (_I, [_P, _I, C.c_longlong]),
+    "grace_trace": (_I, [_P, _I]),
+    "grace_trace_read": (_I, [_P, _DP, C.POINTER(C.c_longlong)]),
     "grace_last_error": (C.c_char_p, [_P]),
     "grace_destroy": (_I, [_P]),
 }

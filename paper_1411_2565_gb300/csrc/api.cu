@@ -51,15 +51,30 @@ constexpr int kEnergyBlocks = 304;
 
 }  // namespace
 
+// Films launched together: either one fast group per (Q, Py, nz) with compile-time FFT
+// lengths, or one generic group (runtime lengths) for everything else.
+struct Group {
+  std::vector<int> idx;
+  bool fast = false;
+  bool fused = true;
+  int Q = 0, Py = 0, nz = 0;
+  int TY = 1, KPB = 1, RPB = 1, TQ = 1;
+  int units[UK_COUNT] = {0, 0, 0, 0, 0};
+  size_t smem_x = 0, smem_yz = 0, smem_y = 0, smem_z = 0;
+  size_t o_desc = 0;
+  std::vector<FilmDev> fd;
+};
+
+enum TraceKind { TK_YZ_FAST = 0, TK_X_FAST, TK_YZ, TK_Y, TK_Z, TK_X, TK_COUNT };
+
 struct grace_ctx {
   std::vector<FilmHost> films;
   std::vector<ShapeClass> classes;
-  std::vector<FilmDev> fd;
+  std::vector<FilmDev> fd;          // all films, film order (energies, per-film updates)
+  std::vector<Group> groups;
+  std::vector<int> film_group;
   long long ncell = 0;
-  bool fused = true;
-  int TY = 1, RPB = 1, TQ = 1;
-  int units[UK_COUNT] = {0, 0, 0, 0, 0};
-  size_t smem_x = 0, smem_yz = 0, smem_y = 0, smem_z = 0;
+  int tile_x = 0, tile_yz = 0;      // 0 = automatic
   size_t o_tw = 0, o_films = 0, o_run = 0, o_m0 = 0, o_m1 = 0, o_H = 0, o_part = 0, o_eout = 0;
   std::vector<size_t> o_S;
   size_t run_bytes = 0, build_bytes = 0, need = 0;
@@ -75,6 +90,12 @@ struct grace_ctx {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   float gdt[2] = {0.f, 0.f};
+  bool trace = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;
+  size_t ev_next = 0;
+  double trace_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long trace_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   std::string err;
 };
 
@@ -114,8 +135,70 @@ bool valid_film(const int n[3], const double cell[3], double Ms, double A, doubl
   return true;
 }
 
-// Choose kernels, tile sizes, unit counts and the workspace layout.
+// Tile sizes, unit counts and dynamic shared memory for one group.
+int plan_group(grace_ctx* c, Group& g) {
+  int maxQ = 1, maxnx = 1, maxny = 1, maxPy = 1, maxPz = 1;
+  g.fused = true;
+  for (int i : g.idx) {
+    const FilmHost& f = c->films[i];
+    const ShapeClass& s = c->classes[f.cls];
+    const size_t slab = (size_t)3 * f.n[2] * line_stride(s.P[1]) * sizeof(float2);
+    if (f.n[2] > 4 || slab > kSmemMax || 3 * f.n[2] * s.P[1] > kTaskCap) g.fused = false;
+    maxQ = std::max(maxQ, s.P[0] / 2);
+    maxnx = std::max(maxnx, f.n[0]);
+    maxny = std::max(maxny, f.n[1]);
+    maxPy = std::max(maxPy, s.P[1]);
+    if (s.zfft) maxPz = std::max(maxPz, s.P[2]);
+  }
+  if (g.fast) {
+    g.fused = true;
+    const int T = g.Q / 8;
+    int TY = c->tile_x > 0 ? c->tile_x : std::min(8, std::max(1, 256 / T));
+    while (TY > 1 && TY * T > 256) TY /= 2;
+    g.TY = TY;
+    g.smem_x = fast_x_smem(g.Q, TY);
+    const int per = 3 * g.nz * (g.Py / 8);
+    int KPB = c->tile_yz > 0 ? c->tile_yz : std::max(1, 256 / per);
+    while (KPB > 1 && KPB * per > 768) --KPB;
+    g.KPB = KPB;
+    g.smem_yz = fast_yz_smem(g.Py, g.nz, KPB);
+    if (g.smem_x > kSmemMax || g.smem_yz > kSmemMax) return GRACE_EUNSUPPORTED;
+  } else {
+    int TY = std::min(8, std::max(1, kTaskCap / std::max(1, maxQ)));
+    TY = std::min(TY, maxny);
+    auto smem_x = [&](int ty) {
+      return (size_t)ty * line_stride(maxQ) * sizeof(float2) + (size_t)3 * ty * maxnx * sizeof(float);
+    };
+    while (TY > 1 && smem_x(TY) > kSmemBudget) --TY;
+    g.TY = TY;
+    g.smem_x = smem_x(TY);
+    g.smem_yz = 0;
+    if (g.fused) {
+      for (int i : g.idx) {
+        const ShapeClass& s = c->classes[c->films[i].cls];
+        g.smem_yz = std::max(g.smem_yz, (size_t)3 * s.n[2] * line_stride(s.P[1]) * sizeof(float2));
+      }
+    }
+    int RPB = std::max(1, kTaskCap / maxPy);
+    while (RPB > 1 && (size_t)RPB * line_stride(maxPy) * sizeof(float2) > kSmemBudget) --RPB;
+    g.RPB = RPB;
+    g.smem_y = (size_t)RPB * line_stride(maxPy) * sizeof(float2);
+    int TQ = kThreadsHost;
+    if (maxPz > 1) {
+      TQ = std::max(1, std::min(32, kTaskCap / (3 * maxPz)));
+      while (TQ > 1 && (size_t)3 * TQ * line_stride(maxPz) * sizeof(float2) > kSmemMax) --TQ;
+    }
+    g.TQ = TQ;
+    g.smem_z = maxPz > 1 ? (size_t)3 * TQ * line_stride(maxPz) * sizeof(float2) : 0;
+    if (g.smem_x > kSmemMax || g.smem_y > kSmemMax || g.smem_z > kSmemMax) return GRACE_EUNSUPPORTED;
+  }
+  return GRACE_OK;
+}
+
+// Choose groups, kernels, tile sizes, unit counts and the workspace layout.
 int plan(grace_ctx* c) {
+  c->classes.clear();
+  c->groups.clear();
   // shape classes (films with identical grid and cell share one tensor)
   for (auto& f : c->films) {
     int k = -1;
@@ -141,55 +224,48 @@ int plan(grace_ctx* c) {
     }
     f.cls = k;
   }
-  // fused y-z pass when every film has nz <= 4 and its slab fits in shared memory
-  c->fused = true;
-  int maxQ = 1, maxnx = 1, maxny = 1, maxPy = 1, maxPz = 1;
-  for (auto& f : c->films) {
+  // groups: fast per (Q, Py, nz), generic for the rest
+  c->film_group.assign(c->films.size(), -1);
+  int generic = -1;
+  for (size_t i = 0; i < c->films.size(); ++i) {
+    const FilmHost& f = c->films[i];
     const ShapeClass& s = c->classes[f.cls];
-    const size_t slab = (size_t)3 * f.n[2] * line_stride(s.P[1]) * sizeof(float2);
-    if (f.n[2] > 4 || slab > kSmemMax || 3 * f.n[2] * s.P[1] > kTaskCap) c->fused = false;
-    maxQ = std::max(maxQ, s.P[0] / 2);
-    maxnx = std::max(maxnx, f.n[0]);
-    maxny = std::max(maxny, f.n[1]);
-    maxPy = std::max(maxPy, s.P[1]);
-    if (s.zfft) maxPz = std::max(maxPz, s.P[2]);
-  }
-  // x pass: TY lines per block
-  int TY = std::min(8, std::max(1, kTaskCap / std::max(1, maxQ)));
-  TY = std::min(TY, maxny);
-  auto smem_x = [&](int ty) {
-    return (size_t)ty * line_stride(maxQ) * sizeof(float2) + (size_t)3 * ty * maxnx * sizeof(float);
-  };
-  while (TY > 1 && smem_x(TY) > kSmemBudget) --TY;
-  c->TY = TY;
-  c->smem_x = smem_x(TY);
-  c->smem_yz = 0;
-  if (c->fused) {
-    for (auto& f : c->films) {
-      const ShapeClass& s = c->classes[f.cls];
-      c->smem_yz = std::max(c->smem_yz, (size_t)3 * f.n[2] * line_stride(s.P[1]) * sizeof(float2));
+    const int Q = s.P[0] / 2, Py = s.P[1], nz = f.n[2];
+    const bool fast = fast_x_supported(Q) && fast_yz_supported(Py, nz);
+    int gi = -1;
+    if (fast) {
+      for (size_t k = 0; k < c->groups.size(); ++k) {
+        const Group& g = c->groups[k];
+        if (g.fast && g.Q == Q && g.Py == Py && g.nz == nz) gi = (int)k;
+      }
+    } else {
+      gi = generic;
     }
+    if (gi < 0) {
+      Group g;
+      g.fast = fast;
+      g.Q = Q;
+      g.Py = Py;
+      g.nz = nz;
+      c->groups.push_back(g);
+      gi = (int)c->groups.size() - 1;
+      if (!fast) generic = gi;
+    }
+    c->groups[gi].idx.push_back((int)i);
+    c->film_group[i] = gi;
   }
-  int RPB = std::max(1, kTaskCap / maxPy);
-  while (RPB > 1 && (size_t)RPB * line_stride(maxPy) * sizeof(float2) > kSmemBudget) --RPB;
-  c->RPB = RPB;
-  c->smem_y = (size_t)RPB * line_stride(maxPy) * sizeof(float2);
-  int TQ = kThreadsHost;
-  if (maxPz > 1) {
-    TQ = std::max(1, std::min(32, kTaskCap / (3 * maxPz)));
-    while (TQ > 1 && (size_t)3 * TQ * line_stride(maxPz) * sizeof(float2) > kSmemMax) --TQ;
+  for (auto& g : c->groups) {
+    int st = plan_group(c, g);
+    if (st != GRACE_OK) return st;
   }
-  c->TQ = TQ;
-  c->smem_z = maxPz > 1 ? (size_t)3 * TQ * line_stride(maxPz) * sizeof(float2) : 0;
-  if (c->smem_x > kSmemMax || c->smem_y > kSmemMax || c->smem_z > kSmemMax) return GRACE_EUNSUPPORTED;
 
-  // per-film descriptors (pointers filled at bind)
+  // per-film descriptors (pointers filled at bind); unit counters are group-local
   c->fd.assign(c->films.size(), FilmDev{});
-  int u[UK_COUNT] = {0, 0, 0, 0, 0};
   long long cell0 = 0;
   for (size_t i = 0; i < c->films.size(); ++i) {
     const FilmHost& h = c->films[i];
     const ShapeClass& s = c->classes[h.cls];
+    const Group& g = c->groups[c->film_group[i]];
     FilmDev& d = c->fd[i];
     d.nx = h.n[0];
     d.ny = h.n[1];
@@ -204,16 +280,7 @@ int plan(grace_ctx* c) {
     d.Kz = s.Kz;
     d.zfft = s.zfft;
     d.nslot = s.nslot;
-    d.srow = c->fused ? d.ny : d.Py;
-    d.u0[UK_X] = u[UK_X];
-    u[UK_X] += d.nz * ((d.ny + TY - 1) / TY);
-    d.u0[UK_YZ] = u[UK_YZ];
-    u[UK_YZ] += d.Kx;
-    d.u0[UK_Y] = u[UK_Y];
-    u[UK_Y] += (3 * d.nz * d.Kx + RPB - 1) / RPB;
-    d.u0[UK_Z] = u[UK_Z];
-    u[UK_Z] += (d.Kx * d.Py + TQ - 1) / TQ;
-    d.u0[UK_CELL] = 0;
+    d.srow = g.fused ? d.ny : d.Py;
     d.cell0 = cell0;
     cell0 += d.ncell;
     d.idx2 = (float)(1.0 / (h.cell[0] * h.cell[0]));
@@ -231,8 +298,23 @@ int plan(grace_ctx* c) {
     d.A = h.A;
     d.Ku = h.Ku;
   }
-  for (int k = 0; k < UK_COUNT; ++k) c->units[k] = u[k];
   c->ncell = cell0;
+  for (auto& g : c->groups) {
+    int u[UK_COUNT] = {0, 0, 0, 0, 0};
+    for (int i : g.idx) {
+      FilmDev& d = c->fd[i];
+      d.u0[UK_X] = u[UK_X];
+      u[UK_X] += d.nz * ((d.ny + g.TY - 1) / g.TY);
+      d.u0[UK_YZ] = u[UK_YZ];
+      u[UK_YZ] += g.fast ? (d.Kx + g.KPB - 1) / g.KPB : d.Kx;
+      d.u0[UK_Y] = u[UK_Y];
+      u[UK_Y] += (3 * d.nz * d.Kx + g.RPB - 1) / g.RPB;
+      d.u0[UK_Z] = u[UK_Z];
+      u[UK_Z] += (d.Kx * d.Py + g.TQ - 1) / g.TQ;
+      d.u0[UK_CELL] = 0;
+    }
+    for (int k = 0; k < UK_COUNT; ++k) g.units[k] = u[k];
+  }
 
   // workspace layout: [twiddles | descriptors | tensors | runtime (aliased by build scratch)]
   size_t o = 0;
@@ -240,6 +322,10 @@ int plan(grace_ctx* c) {
   o = al256(o + (size_t)GRACE_LMAX * sizeof(float2));
   c->o_films = o;
   o = al256(o + c->films.size() * sizeof(FilmDev));
+  for (auto& g : c->groups) {
+    g.o_desc = o;
+    o = al256(o + g.idx.size() * sizeof(FilmDev));
+  }
   for (auto& s : c->classes) {
     s.t_off = o;
     o = al256(o + (size_t)s.Kx * s.nslot * s.Ky * sizeof(float));
@@ -289,62 +375,145 @@ void fill_pointers(grace_ctx* c) {
     d.ms_field = c->ms_field ? c->ms_field + d.cell0 : nullptr;
     d.h_field = c->h_field ? c->h_field + 3 * d.cell0 : nullptr;
   }
+  for (auto& g : c->groups) {
+    g.fd.clear();
+    for (int i : g.idx) g.fd.push_back(c->fd[i]);
+  }
 }
 
 int upload_films(grace_ctx* c) {
   GRACE_CUDA(c, cudaMemcpyAsync(c->ws + c->o_films, c->fd.data(), c->fd.size() * sizeof(FilmDev),
                                 cudaMemcpyHostToDevice, c->stream));
+  for (auto& g : c->groups) {
+    GRACE_CUDA(c, cudaMemcpyAsync(c->ws + g.o_desc, g.fd.data(), g.fd.size() * sizeof(FilmDev),
+                                  cudaMemcpyHostToDevice, c->stream));
+  }
   return GRACE_OK;
 }
 
-LaunchP base_lp(const grace_ctx* c) {
+LaunchP group_lp(const grace_ctx* c, const Group& g) {
   LaunchP lp{};
-  lp.nfilms = (int)c->films.size();
+  lp.nfilms = (int)g.idx.size();
   lp.parity = c->parity;
   lp.dt = 0.f;
   lp.mask = 15u;
   lp.out = nullptr;
-  lp.TY = c->TY;
-  lp.RPB = c->RPB;
-  lp.TQ = c->TQ;
+  lp.TY = g.TY;
+  lp.RPB = g.RPB;
+  lp.TQ = g.TQ;
   lp.tw = reinterpret_cast<const float2*>(c->ws + c->o_tw);
   return lp;
+}
+
+const FilmDev* gfilms(const grace_ctx* c, const Group& g) {
+  return reinterpret_cast<const FilmDev*>(c->ws + g.o_desc);
 }
 
 const FilmDev* dfilms(const grace_ctx* c) {
   return reinterpret_cast<const FilmDev*>(c->ws + c->o_films);
 }
 
-cudaError_t enqueue_conv(const grace_ctx* c, const LaunchP& lp, cudaStream_t s) {
-  const FilmDev* f = dfilms(c);
-  if (c->fused) return launch_yz(f, lp, c->units[UK_YZ], c->smem_yz, s);
-  cudaError_t e = launch_y(-1, f, lp, c->units[UK_Y], c->smem_y, s);
-  if (e != cudaSuccess) return e;
-  e = launch_z(f, lp, c->units[UK_Z], c->smem_z, s);
-  if (e != cudaSuccess) return e;
-  return launch_y(+1, f, lp, c->units[UK_Y], c->smem_y, s);
+// Optional per-kernel timing: an event pair around each launch on the launch stream.
+cudaError_t mark(grace_ctx* c, int kind, cudaStream_t s) {
+  if (!c->trace) return cudaSuccess;
+  if (c->ev_next == c->ev.size()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    c->ev.push_back(e);
+    c->ev_kind.push_back(kind);
+  }
+  c->ev_kind[c->ev_next] = kind;
+  return cudaEventRecord(c->ev[c->ev_next++], s);
 }
 
-cudaError_t enqueue_step(const grace_ctx* c, int parity, float dt, cudaStream_t s) {
-  LaunchP lp = base_lp(c);
-  lp.parity = parity;
-  lp.dt = dt;
-  cudaError_t e = enqueue_conv(c, lp, s);
-  if (e != cudaSuccess) return e;
-  return launch_xpass(XM_STEP, dfilms(c), lp, c->units[UK_X], c->smem_x, s);
+#define GRACE_LAUNCH(c, kind, s, call)                 \
+  do {                                                 \
+    cudaError_t e_ = mark(c, kind, s);                 \
+    if (e_ == cudaSuccess) e_ = (call);                \
+    if (e_ == cudaSuccess) e_ = mark(c, kind, s);      \
+    if (e_ != cudaSuccess) return e_;                  \
+  } while (0)
+
+cudaError_t enqueue_conv(grace_ctx* c, const Group& g, const LaunchP& lp, cudaStream_t s) {
+  const FilmDev* f = gfilms(c, g);
+  if (g.fast) {
+    GRACE_LAUNCH(c, TK_YZ_FAST, s, launch_fast_yz(g.Py, g.nz, f, lp, g.units[UK_YZ], g.KPB, g.smem_yz, s));
+    return cudaSuccess;
+  }
+  if (g.fused) {
+    GRACE_LAUNCH(c, TK_YZ, s, launch_yz(f, lp, g.units[UK_YZ], g.smem_yz, s));
+    return cudaSuccess;
+  }
+  GRACE_LAUNCH(c, TK_Y, s, launch_y(-1, f, lp, g.units[UK_Y], g.smem_y, s));
+  GRACE_LAUNCH(c, TK_Z, s, launch_z(f, lp, g.units[UK_Z], g.smem_z, s));
+  GRACE_LAUNCH(c, TK_Y, s, launch_y(+1, f, lp, g.units[UK_Y], g.smem_y, s));
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_x(grace_ctx* c, const Group& g, int mode, const LaunchP& lp, cudaStream_t s) {
+  const FilmDev* f = gfilms(c, g);
+  if (g.fast) {
+    GRACE_LAUNCH(c, TK_X_FAST, s, launch_fast_x(g.Q, mode, f, lp, g.units[UK_X], g.TY, g.smem_x, s));
+  } else {
+    GRACE_LAUNCH(c, TK_X, s, launch_xpass(mode, f, lp, g.units[UK_X], g.smem_x, s));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_step(grace_ctx* c, int parity, float dt, cudaStream_t s) {
+  for (const auto& g : c->groups) {
+    LaunchP lp = group_lp(c, g);
+    lp.parity = parity;
+    lp.dt = dt;
+    cudaError_t e = enqueue_conv(c, g, lp, s);
+    if (e != cudaSuccess) return e;
+    e = enqueue_x(c, g, XM_STEP, lp, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_r2c(grace_ctx* c) {
+  for (const auto& g : c->groups) {
+    LaunchP lp = group_lp(c, g);
+    cudaError_t e = enqueue_x(c, g, XM_R2C, lp, c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int enqueue_heff(grace_ctx* c, float* out, unsigned mask) {
-  LaunchP lp = base_lp(c);
-  lp.mask = mask;
-  lp.out = out;
-  if (mask & GRACE_TERM_DEMAG) {
-    cudaError_t e = enqueue_conv(c, lp, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "demag convolution launch");
+  for (const auto& g : c->groups) {
+    LaunchP lp = group_lp(c, g);
+    lp.mask = mask;
+    lp.out = out;
+    if (mask & GRACE_TERM_DEMAG) {
+      cudaError_t e = enqueue_conv(c, g, lp, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "demag convolution launch");
+    }
+    cudaError_t e = enqueue_x(c, g, XM_HEFF, lp, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "x pass launch");
   }
-  cudaError_t e = launch_xpass(XM_HEFF, dfilms(c), lp, c->units[UK_X], c->smem_x, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "x pass launch");
   return GRACE_OK;
+}
+
+cudaError_t configure_all(grace_ctx* c) {
+  size_t sx = 0, syz = 0, sy = 0, sz = 0;
+  for (const auto& g : c->groups) {
+    cudaError_t e = cudaSuccess;
+    if (g.fast) {
+      e = configure_fast_x(g.Q, std::max<size_t>(g.smem_x, 1));
+      if (e == cudaSuccess) e = configure_fast_yz(g.Py, g.nz, std::max<size_t>(g.smem_yz, 1));
+      if (e != cudaSuccess) return e;
+    } else {
+      sx = std::max(sx, g.smem_x);
+      syz = std::max(syz, g.smem_yz);
+      sy = std::max(sy, g.smem_y);
+      sz = std::max(sz, g.smem_z);
+    }
+  }
+  return configure_kernels(sx, syz, sy, sz);
 }
 
 void drop_graphs(grace_ctx* c) {
@@ -362,11 +531,6 @@ int ready(grace_ctx* c, bool need_m) {
 }
 
 }  // namespace
-
-// Kernel attribute setup lives with the kernels; declared here.
-namespace grace {
-cudaError_t configure_kernels(size_t smem_x, size_t smem_yz, size_t smem_y, size_t smem_z);
-}
 
 extern "C" {
 
@@ -439,7 +603,7 @@ int grace_bind(grace_ctx* c, void* dev_ws, size_t bytes, void* cuda_stream) {
   c->bound = false;
   c->mset = false;
   c->parity = 0;
-  GRACE_CUDA(c, configure_kernels(c->smem_x, c->smem_yz, c->smem_y, c->smem_z));
+  GRACE_CUDA(c, configure_all(c));
   // twiddle table exp(-2 pi i m / LMAX), FP64 on the host, rounded to FP32
   std::vector<float2> tw(GRACE_LMAX);
   for (int m = 0; m < GRACE_LMAX; ++m) {
@@ -510,8 +674,7 @@ int grace_set_m(grace_ctx* c, const float* dev_m) {
   float* dst = reinterpret_cast<float*>(c->ws + c->o_run + (c->parity ? c->o_m1 : c->o_m0));
   GRACE_CUDA(c, cudaMemcpyAsync(dst, dev_m, (size_t)3 * c->ncell * sizeof(float),
                                 cudaMemcpyDeviceToDevice, c->stream));
-  LaunchP lp = base_lp(c);
-  GRACE_CUDA(c, launch_xpass(XM_R2C, dfilms(c), lp, c->units[UK_X], c->smem_x, c->stream));
+  GRACE_CUDA(c, enqueue_r2c(c));
   c->mset = true;
   return GRACE_OK;
 }
@@ -523,8 +686,7 @@ int grace_set_m_host(grace_ctx* c, const float* host_m) {
   float* dst = reinterpret_cast<float*>(c->ws + c->o_run + (c->parity ? c->o_m1 : c->o_m0));
   GRACE_CUDA(c, cudaMemcpyAsync(dst, host_m, (size_t)3 * c->ncell * sizeof(float),
                                 cudaMemcpyHostToDevice, c->stream));
-  LaunchP lp = base_lp(c);
-  GRACE_CUDA(c, launch_xpass(XM_R2C, dfilms(c), lp, c->units[UK_X], c->smem_x, c->stream));
+  GRACE_CUDA(c, enqueue_r2c(c));
   c->mset = true;
   return GRACE_OK;
 }
@@ -570,7 +732,10 @@ int grace_set_film_hext(grace_ctx* c, int film, const double h[3]) {
   c->fd[film].hx = (float)h[0];
   c->fd[film].hy = (float)h[1];
   c->fd[film].hz = (float)h[2];
-  if (c->bound) return upload_films(c);
+  if (c->bound) {
+    fill_pointers(c);
+    return upload_films(c);
+  }
   return GRACE_OK;
 }
 
@@ -589,10 +754,7 @@ int grace_set_ms_field(grace_ctx* c, const float* dev_ms) {
   fill_pointers(c);
   st = upload_films(c);
   if (st) return st;
-  if (c->mset) {   // the spectrum holds FFT(Ms m): refresh it
-    LaunchP lp = base_lp(c);
-    GRACE_CUDA(c, launch_xpass(XM_R2C, dfilms(c), lp, c->units[UK_X], c->smem_x, c->stream));
-  }
+  if (c->mset) GRACE_CUDA(c, enqueue_r2c(c));   // the spectrum holds FFT(Ms m): refresh it
   return GRACE_OK;
 }
 
@@ -612,7 +774,7 @@ int grace_step(grace_ctx* c, int n, double dt) {
   const float fdt = (float)dt;
   int done = 0;
   const int G = c->graph_steps;
-  if (c->use_graph && c->cap && n >= G) {
+  if (c->use_graph && c->cap && !c->trace && n >= G) {
     const int p = c->parity;
     if (!c->gexec[p] || c->gdt[p] != fdt) {
       if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
@@ -650,7 +812,9 @@ int grace_energy(grace_ctx* c, double out[5], double mavg[3]) {
   float* H = reinterpret_cast<float*>(c->ws + c->o_run + c->o_H);
   st = enqueue_heff(c, H, GRACE_TERM_DEMAG);
   if (st) return st;
-  LaunchP lp = base_lp(c);
+  LaunchP lp{};
+  lp.nfilms = (int)c->films.size();
+  lp.parity = c->parity;
   double* part = reinterpret_cast<double*>(c->ws + c->o_run + c->o_part);
   double* res = reinterpret_cast<double*>(c->ws + c->o_run + c->o_eout);
   GRACE_CUDA(c, launch_energy(dfilms(c), lp, H, c->ncell, part, kEnergyBlocks, res, c->stream));
@@ -692,6 +856,21 @@ int grace_set_option(grace_ctx* c, int option, long long value) {
       if (c->use_graph && c->bound && !c->cap)
         GRACE_CUDA(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
       return GRACE_OK;
+    case GRACE_OPT_TILE_X:
+    case GRACE_OPT_TILE_YZ: {
+      if (c->bound) return fail(c, GRACE_ESTATE, "tile options must be set before grace_bind");
+      if (value < 0 || value > 64) return fail(c, GRACE_EINVAL, "tile option out of range 0..64");
+      const int old_x = c->tile_x, old_yz = c->tile_yz;
+      (option == GRACE_OPT_TILE_X ? c->tile_x : c->tile_yz) = (int)value;
+      const int st = plan(c);
+      if (st != GRACE_OK) {
+        c->tile_x = old_x;
+        c->tile_yz = old_yz;
+        plan(c);
+        return fail(c, st, "tile option not supported for this shape");
+      }
+      return GRACE_OK;
+    }
     case GRACE_OPT_GRAPH_STEPS:
       if (value < 2 || value > 4096 || (value & 1)) return fail(c, GRACE_EINVAL, "graph steps: even, 2..4096");
       c->graph_steps = (int)value;
@@ -702,12 +881,43 @@ int grace_set_option(grace_ctx* c, int option, long long value) {
   }
 }
 
+int grace_trace(grace_ctx* c, int on) {
+  if (!c || (on != 0 && on != 1)) return GRACE_EINVAL;
+  c->trace = on != 0;
+  c->ev_next = 0;
+  for (int k = 0; k < 8; ++k) {
+    c->trace_ms[k] = 0.0;
+    c->trace_n[k] = 0;
+  }
+  return GRACE_OK;
+}
+
+int grace_trace_read(grace_ctx* c, double ms[8], long long counts[8]) {
+  if (!c || !ms || !counts) return GRACE_EINVAL;
+  if (c->ev_next > 0) GRACE_CUDA(c, cudaEventSynchronize(c->ev[c->ev_next - 1]));
+  for (size_t i = 0; i + 1 < c->ev_next; i += 2) {
+    float t = 0.f;
+    GRACE_CUDA(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
+    c->trace_ms[c->ev_kind[i]] += t;
+    c->trace_n[c->ev_kind[i]] += 1;
+  }
+  c->ev_next = 0;
+  for (int k = 0; k < 8; ++k) {
+    ms[k] = c->trace_ms[k];
+    counts[k] = c->trace_n[k];
+    c->trace_ms[k] = 0.0;
+    c->trace_n[k] = 0;
+  }
+  return GRACE_OK;
+}
+
 const char* grace_last_error(const grace_ctx* c) { return c ? c->err.c_str() : "null handle"; }
 
 int grace_destroy(grace_ctx* c) {
   if (!c) return GRACE_OK;
   drop_graphs(c);
   if (c->cap) cudaStreamDestroy(c->cap);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   delete c;
   return GRACE_OK;
 }

@@ -1,0 +1,194 @@
+// Fused y pass for films with nz <= 4 and compile-time Py >= 8: per kx column, the y FFT
+// of the 3 nz rows of S (zero-padded from ny to Py), the k-space tensor product with a
+// direct sum along z (the zero-padded z convolution of Sec. 3 written out for thin
+// films), the inverse y FFT and the crop back to ny rows.
+//
+// Block = KPB kx columns x 3 nz lines x Py/8 threads per line.  The forward FFT starts
+// from registers loaded straight from S and the inverse ends in registers stored
+// straight to S; shared memory carries the FFT exchanges and the transpose that gives
+// one thread all 3 nz values of one (kx, ky) for the tensor product.
+#include <cuda_runtime.h>
+
+#include "fftreg.cuh"
+#include "internal.cuh"
+
+namespace grace {
+namespace {
+
+template <int NZ>
+__device__ __forceinline__ void tensor_product(const float* __restrict__ Tk, int Ky, float sy,
+                                               float2 (&M)[3][NZ], float2 (&H)[3][NZ]) {
+  constexpr int NS = NZ == 1 ? 4 : 6 * NZ - 2;
+  float t[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) t[s] = __ldg(Tk + (size_t)s * Ky);
+#pragma unroll
+  for (int z = 0; z < NZ; ++z) {
+    float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
+#pragma unroll
+    for (int zp = 0; zp < NZ; ++zp) {
+      const int dz = z - zp;
+      const int a = dz >= 0 ? dz : -dz;
+      const float sz = dz >= 0 ? 1.f : -1.f;
+      const float nxx = t[4 * a], nyy = t[4 * a + 1], nzz = t[4 * a + 2], nxy = sy * t[4 * a + 3];
+      const float2 mx = M[0][zp], my = M[1][zp], mz = M[2][zp];
+      hx.x = fmaf(nxx, mx.x, fmaf(nxy, my.x, hx.x));
+      hx.y = fmaf(nxx, mx.y, fmaf(nxy, my.y, hx.y));
+      hy.x = fmaf(nxy, mx.x, fmaf(nyy, my.x, hy.x));
+      hy.y = fmaf(nxy, mx.y, fmaf(nyy, my.y, hy.y));
+      hz.x = fmaf(nzz, mz.x, hz.x);
+      hz.y = fmaf(nzz, mz.y, hz.y);
+      if (a > 0) {
+        // xz and yz are imaginary at a z offset: i t
+        const float txz = sz * t[4 * NZ + 2 * (a - 1)];
+        const float tyz = sy * sz * t[4 * NZ + 2 * (a - 1) + 1];
+        hx.x = fmaf(-txz, mz.y, hx.x);
+        hx.y = fmaf(txz, mz.x, hx.y);
+        hy.x = fmaf(-tyz, mz.y, hy.x);
+        hy.y = fmaf(tyz, mz.x, hy.y);
+        hz.x = fmaf(-txz, mx.y, fmaf(-tyz, my.y, hz.x));
+        hz.y = fmaf(txz, mx.x, fmaf(tyz, my.x, hz.y));
+      }
+    }
+    H[0][z] = hx;
+    H[1][z] = hy;
+    H[2][z] = hz;
+  }
+}
+
+template <int PY, int NZ>
+__global__ void __launch_bounds__(768) kyz_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+  constexpr int T = PY / 8;
+  constexpr int NL = 3 * NZ;
+  constexpr int LS = fast_line_stride(PY, T);
+  const int KPB = blockDim.x / (NL * T);
+  const int tid = threadIdx.x;
+  const int j = tid % T;
+  const int li = tid / T;             // kxi * NL + line
+  const int line = li % NL;
+  const int kxi = li / NL;
+  const int unit = blockIdx.x;
+  const FilmDev& f = films[find_film(films, lp.nfilms, UK_YZ, unit)];
+  const int kx0 = (unit - f.u0[UK_YZ]) * KPB;
+  const int kx = kx0 + kxi;
+  const bool ok = kx < f.Kx;
+  const int ny = f.ny;
+  extern __shared__ float4 smem4[];
+  float2* sm = reinterpret_cast<float2*>(smem4);
+  float2* buf = sm + li * LS;
+  float2* S = f.S + ((size_t)line * f.Kx + kx) * f.srow;
+
+  float2 v[8];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int y = j + r * T;
+    v[r] = (ok && y < ny) ? S[y] : make_float2(0.f, 0.f);
+    v[r + 4] = make_float2(0.f, 0.f);
+  }
+  fft_reg<PY, -1, true>(v, j, buf, lp.tw);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) buf[pad16(j + r * T)] = v[r];
+  __syncthreads();
+
+  const int npair = KPB * PY;
+  for (int p = tid; p < npair; p += blockDim.x) {
+    const int ki = p / PY, ky = p - ki * PY;
+    const int kxx = kx0 + ki;
+    if (kxx >= f.Kx) continue;
+    const bool lo = ky <= PY / 2;
+    const int kyp = lo ? ky : PY - ky;
+    const float sy = lo ? 1.f : -1.f;
+    float2 M[3][NZ], H[3][NZ];
+    float2* base = sm + (size_t)ki * NL * LS + pad16(ky);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) M[c][z] = base[(c * NZ + z) * LS];
+    tensor_product<NZ>(f.T + (size_t)kxx * f.nslot * f.Ky + kyp, f.Ky, sy, M, H);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) base[(c * NZ + z) * LS] = H[c][z];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = buf[pad16(j + r * T)];
+  __syncthreads();
+  fft_reg<PY, +1, false>(v, j, buf, lp.tw);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int y = j + r * T;
+    if (ok && y < ny) S[y] = v[r];
+  }
+}
+
+template <int PY, int NZ>
+constexpr bool yz_ok() {
+  return 3 * NZ * (PY / 8) <= 768;
+}
+
+template <int PY, int NZ>
+cudaError_t launch_pn(const FilmDev* films, const LaunchP& lp, int nunits, int threads, size_t smem,
+                      cudaStream_t s, bool attr_only) {
+  if constexpr (yz_ok<PY, NZ>()) {
+    if (attr_only)
+      return cudaFuncSetAttribute((const void*)kyz_fast<PY, NZ>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kyz_fast<PY, NZ><<<nunits, threads, smem, s>>>(films, lp);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <int PY>
+cudaError_t launch_p(int nz, const FilmDev* films, const LaunchP& lp, int nunits, int threads, size_t smem,
+                     cudaStream_t s, bool attr_only) {
+  switch (nz) {
+    case 1: return launch_pn<PY, 1>(films, lp, nunits, threads, smem, s, attr_only);
+    case 2: return launch_pn<PY, 2>(films, lp, nunits, threads, smem, s, attr_only);
+    case 3: return launch_pn<PY, 3>(films, lp, nunits, threads, smem, s, attr_only);
+    case 4: return launch_pn<PY, 4>(films, lp, nunits, threads, smem, s, attr_only);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t dispatch(int Py, int nz, const FilmDev* films, const LaunchP& lp, int nunits, int threads,
+                     size_t smem, cudaStream_t s, bool attr_only) {
+  switch (Py) {
+    case 8: return launch_p<8>(nz, films, lp, nunits, threads, smem, s, attr_only);
+    case 16: return launch_p<16>(nz, films, lp, nunits, threads, smem, s, attr_only);
+    case 32: return launch_p<32>(nz, films, lp, nunits, threads, smem, s, attr_only);
+    case 64: return launch_p<64>(nz, films, lp, nunits, threads, smem, s, attr_only);
+    case 128: return launch_p<128>(nz, films, lp, nunits, threads, smem, s, attr_only);
+    case 256: return launch_p<256>(nz, films, lp, nunits, threads, smem, s, attr_only);
+    case 512: return launch_p<512>(nz, films, lp, nunits, threads, smem, s, attr_only);
+    case 1024: return launch_p<1024>(nz, films, lp, nunits, threads, smem, s, attr_only);
+    case 2048: return launch_p<2048>(nz, films, lp, nunits, threads, smem, s, attr_only);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+bool fast_yz_supported(int Py, int nz) {
+  return Py >= 8 && Py <= 2048 && nz >= 1 && nz <= 4 && 3 * nz * (Py / 8) <= 768;
+}
+
+size_t fast_yz_smem(int Py, int nz, int kpb) {
+  return (size_t)kpb * 3 * nz * fast_line_stride(Py, Py / 8) * sizeof(float2);
+}
+
+cudaError_t configure_fast_yz(int Py, int nz, size_t smem) {
+  LaunchP lp{};
+  return dispatch(Py, nz, nullptr, lp, 0, 0, smem, nullptr, true);
+}
+
+cudaError_t launch_fast_yz(int Py, int nz, const FilmDev* films, const LaunchP& lp, int nunits, int kpb,
+                           size_t smem, cudaStream_t s) {
+  if (nunits <= 0) return cudaSuccess;
+  const int threads = kpb * 3 * nz * (Py / 8);
+  return dispatch(Py, nz, films, lp, nunits, threads, smem, s, false);
+}
+
+}  // namespace grace

@@ -22,7 +22,7 @@
 namespace grace {
 
 __device__ __forceinline__ int padi(int i) { return i + (i >> 5); }
-__host__ __device__ __forceinline__ int line_stride(int L) { return L + (L >> 5) + 1; }
+__host__ __device__ constexpr int line_stride(int L) { return L + (L >> 5) + 1; }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

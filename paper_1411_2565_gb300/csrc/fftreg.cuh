@@ -1,0 +1,140 @@
+// Register-resident Stockham FFT of compile-time length L (8 <= L <= GRACE_LMAX).
+//
+// Thread j (0 <= j < L/8) of a line holds v[s] = x[j + s L/8], s = 0..7.  Radix-8
+// stages run on those registers; between stages the values move through the line's
+// shared-memory buffer.  With radix-8 stages first and at most one radix-4 or radix-2
+// stage last, the outputs come back in the same distribution: v[s] = X[j + s L/8].  A
+// transform can therefore start from values loaded straight from global memory and
+// hand its outputs straight to the next computation.
+//
+// Bank layout: 16 consecutive threads of a line issue one 64-bit shared access each.
+// Reads of the next stage's inputs touch consecutive j, so any padding that is constant
+// over aligned 16-element blocks keeps them conflict-free.  The scattered writes of a
+// stage with stride NS need more: after NS = 1 (thread j writes 8j + r) one pad element
+// per 16 (pad16) spreads 16 threads over 16 bank pairs; after NS = 8 (threads j and j+8
+// write 64 apart) a shift of 8 bank pairs per 64 elements (pad64) does; later stages
+// write consecutive runs of at least 16.  line_stride covers both layouts.
+//
+// ZERO_UPPER: x[L/2..L-1] are zero (zero padding): the first stage treats v[4..7] as 0.
+// Every thread of the block must call with the same L (the exchanges use
+// __syncthreads()); the caller syncs before the first exchange reuses a buffer that
+// other threads may still be reading.
+#pragma once
+#include "fft.cuh"
+
+namespace grace {
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__device__ __forceinline__ int pad64(int i) { return i + ((i >> 6) << 3); }
+// float2 elements per line buffer (both layouts), rounded so that consecutive lines start
+// `shift` bank pairs apart (shift = 16 / lines-sharing-a-half-warp).
+__host__ __device__ constexpr int fast_line_stride(int L, int shift) {
+  return ((L + L / 8 + 1 + 15) / 16) * 16 + (shift & 15);
+}
+
+template <int NS> __device__ __forceinline__ int padx(int i) {
+  if constexpr (NS == 8) return pad64(i);
+  else return pad16(i);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft8_upper_zero(float2* v) {
+  // inputs v[4..7] are zero: E = DFT4(v0, v2, 0, 0), O = DFT4(v1, v3, 0, 0)
+  const float2 e0 = cadd(v[0], v[2]), e2 = csub(v[0], v[2]);
+  const float2 e1 = cadd(v[0], mul_w4<DIR>(v[2])), e3 = csub(v[0], mul_w4<DIR>(v[2]));
+  const float2 o0 = cadd(v[1], v[3]), o2 = csub(v[1], v[3]);
+  const float2 o1 = cadd(v[1], mul_w4<DIR>(v[3])), o3 = csub(v[1], mul_w4<DIR>(v[3]));
+  const float r = 0.70710678118654752440f;
+  const float2 t1 = DIR < 0 ? make_float2((o1.x + o1.y) * r, (o1.y - o1.x) * r)
+                            : make_float2((o1.x - o1.y) * r, (o1.y + o1.x) * r);
+  const float2 t2 = mul_w4<DIR>(o2);
+  const float2 t3 = DIR < 0 ? make_float2((o3.y - o3.x) * r, -(o3.x + o3.y) * r)
+                            : make_float2(-(o3.x + o3.y) * r, (o3.x - o3.y) * r);
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, t1);
+  v[5] = csub(e1, t1);
+  v[2] = cadd(e2, t2);
+  v[6] = csub(e2, t2);
+  v[3] = cadd(e3, t3);
+  v[7] = csub(e3, t3);
+}
+
+// v[r] *= w^r for r = 1..7, w = table[m]: three table loads (w, w^2, w^4), four products.
+template <int DIR>
+__device__ __forceinline__ void twiddle8(float2 (&v)[8], const float2* __restrict__ tw, int m) {
+  const float2 w1 = twiddle<DIR>(tw, m);
+  const float2 w2 = twiddle<DIR>(tw, 2 * m);
+  const float2 w4 = twiddle<DIR>(tw, 4 * m);
+  const float2 w3 = cmul(w1, w2);
+  v[1] = cmul(v[1], w1);
+  v[2] = cmul(v[2], w2);
+  v[3] = cmul(v[3], w3);
+  v[4] = cmul(v[4], w4);
+  v[5] = cmul(v[5], cmul(w1, w4));
+  v[6] = cmul(v[6], cmul(w2, w4));
+  v[7] = cmul(v[7], cmul(w3, w4));
+}
+
+template <int L, int NS, int DIR, bool FIRST, bool ZU>
+__device__ __forceinline__ void fft_reg_stage(float2 (&v)[8], int j, float2* sm,
+                                              const float2* __restrict__ tw) {
+  constexpr int L8 = L / 8;
+  constexpr int REM = L / NS;
+  constexpr int R = REM >= 8 ? 8 : REM;
+  constexpr bool LAST = (NS * R == L);
+  constexpr int TWS = GRACE_LMAX / (NS * R);
+  if constexpr (R == 8) {
+    const int k = j & (NS - 1);
+    if constexpr (NS > 1) twiddle8<DIR>(v, tw, k * TWS);
+    if constexpr (FIRST && ZU) dft8_upper_zero<DIR>(v);
+    else dft8<DIR>(v);
+    if constexpr (!LAST) {
+      const int o = (j - k) * 8 + k;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) sm[padx<NS>(o + r * NS)] = v[r];
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < 8; ++s) v[s] = sm[padx<NS>(j + s * L8)];
+      __syncthreads();
+      fft_reg_stage<L, NS * 8, DIR, false, ZU>(v, j, sm, tw);
+    }
+  } else if constexpr (R == 4) {
+    // last stage (NS = L/4): butterflies jj = j + b L/8 on v[2r + b]; outputs return in place
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int k = j + b * L8;
+      float2 a0 = v[b], a1 = v[2 + b], a2 = v[4 + b], a3 = v[6 + b];
+      if constexpr (NS > 1) {
+        const float2 w1 = twiddle<DIR>(tw, k * TWS), w2 = twiddle<DIR>(tw, 2 * k * TWS);
+        a1 = cmul(a1, w1);
+        a2 = cmul(a2, w2);
+        a3 = cmul(a3, cmul(w1, w2));
+      }
+      dft4<DIR>(a0, a1, a2, a3);
+      v[b] = a0;
+      v[2 + b] = a1;
+      v[4 + b] = a2;
+      v[6 + b] = a3;
+    }
+  } else {
+    // last stage (NS = L/2): butterflies jj = j + b L/8 on (v[b], v[b + 4])
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int k = j + b * L8;
+      float2 a0 = v[b], a1 = v[b + 4];
+      if constexpr (NS > 1) a1 = cmul(a1, twiddle<DIR>(tw, k * TWS));
+      dft2<DIR>(a0, a1);
+      v[b] = a0;
+      v[b + 4] = a1;
+    }
+  }
+}
+
+template <int L, int DIR, bool ZU>
+__device__ __forceinline__ void fft_reg(float2 (&v)[8], int j, float2* sm, const float2* __restrict__ tw) {
+  static_assert(L >= 8 && (L & (L - 1)) == 0 && L <= GRACE_LMAX, "power-of-two length 8..LMAX");
+  fft_reg_stage<L, 1, DIR, true, ZU>(v, j, sm, tw);
+}
+
+}  // namespace grace

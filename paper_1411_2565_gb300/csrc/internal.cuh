@@ -89,6 +89,19 @@ cudaError_t launch_energy(const FilmDev* films, const LaunchP& lp, const float* 
                           long long ntotal, double* partial, int nblocks, double* result,
                           cudaStream_t s);
 
+// Fast kernels with compile-time FFT lengths (fastx.cu, fastyz.cu).
+bool fast_x_supported(int Q);
+size_t fast_x_smem(int Q, int TY);
+cudaError_t configure_fast_x(int Q, size_t smem);
+cudaError_t launch_fast_x(int Q, int mode, const FilmDev* films, const LaunchP& lp, int nunits, int TY,
+                          size_t smem, cudaStream_t s);
+bool fast_yz_supported(int Py, int nz);
+size_t fast_yz_smem(int Py, int nz, int kpb);
+cudaError_t configure_fast_yz(int Py, int nz, size_t smem);
+cudaError_t launch_fast_yz(int Py, int nz, const FilmDev* films, const LaunchP& lp, int nunits, int kpb,
+                           size_t smem, cudaStream_t s);
+cudaError_t configure_kernels(size_t smem_x, size_t smem_yz, size_t smem_y, size_t smem_z);
+
 struct TensorJob {
   int nx, ny, nz, Px, Py, Pz, Kx, Ky, Kz, zfft, nslot;
   double dx, dy, dz;

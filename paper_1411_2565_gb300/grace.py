@@ -87,6 +87,16 @@ class _Base:
         check(self._L.grace_set_ms_field(self.ctx, ptr), "grace_set_ms_field", self.ctx)
         self._keep["ms"] = ms
 
+    def trace(self, on: bool = True):
+        check(self._L.grace_trace(self.ctx, 1 if on else 0), "grace_trace", self.ctx)
+
+    def trace_read(self):
+        """{kernel kind: (total ms, launches)} since the last read (see GRACE_KERNEL_*)."""
+        ms = (C.c_double * 8)()
+        n = (C.c_longlong * 8)()
+        check(self._L.grace_trace_read(self.ctx, ms, n), "grace_trace_read", self.ctx)
+        return {name: (ms[k], int(n[k])) for k, name in enumerate(_lib.KERNEL_NAMES) if n[k]}
+
     def set_option(self, option: int, value: int):
         check(self._L.grace_set_option(self.ctx, option, value), "grace_set_option", self.ctx)
 
