@@ -1,0 +1,345 @@
+"""Benchmark: LLG cell-steps/s of the full H_eff + Euler step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grace|reference]
+                    [--workload film_large|block|film_small]
+
+One "step" is one pass of the hot path over the film: demag convolution (fused y pass
+and x C2R), exchange, anisotropy, Zeeman, explicit Euler with renormalisation and the
+x R2C of the new state (two kernels per step).  Inputs are resident in HBM when the
+timed region starts; every timed step is preceded by an L2 flush (a 256 MiB write)
+because the film's working set (~100 MB) fits in the 129 MB L2.
+
+For N > 1 (torchrun, one process per GPU) every rank steps its own replica of the film
+(replicas only: the workload has no data exchange), value = all ranks' cell-steps / the
+slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle (the only reference
+implementation: the paper's own code is not available) on rank 0.
+
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LLG cell-steps/s on 1 GB300 (full H_eff + step), % HBM roofline, vs oracle"
+UNIT = "cell-steps/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="grace", choices=["grace", "reference"])
+    ap.add_argument("--workload", default="film_large", choices=["film_large", "block", "film_small"])
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    csrc = os.path.join(ROOT, "paper_1411_2565_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernels are unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("kernels", {}).get(workload, {}).get(kernel)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.rows = []
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.p.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def algorithmic_bytes(g, film):
+    """Compulsory bytes of one launch of each kernel (each operand read once, result written once)."""
+    nx, ny, nz = film.grid
+    Px = 1
+    while Px < 2 * nx - 1:
+        Px *= 2
+    Py = 1
+    while Py < 2 * ny - 1:
+        Py *= 2
+    Kx, Ky = Px // 2 + 1, Py // 2 + 1
+    nslot = 4 if nz == 1 else 6 * nz - 2
+    N = nx * ny * nz
+    spec = 3 * nz * Kx * ny * 8
+    tensor = Kx * nslot * Ky * 4
+    return {"yz_fast": 2 * spec + tensor,          # read S and T, write S
+            "x_fast": 2 * spec + 2 * 12 * N,       # read S and m, write S and m
+            "per_cell": (4 * spec + tensor + 24 * N) / N}
+
+
+def run_grace(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_1411_2565_gb300 import build as libbuild
+    from paper_1411_2565_gb300.grace import Grace
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    libbuild.build()
+    w = getattr(workloads, args.workload)()
+    f, m0 = w.films[0], w.m0[0]
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=dev)
+    g.set_hext(f.hext)
+    m_dev = torch.from_numpy(m0.reshape(-1)).to(dev)
+    g.set_m(m_dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        g.step(1, w.dt)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    g.trace(4 * args.steps + 8)          # events for every launch of the timed loop
+    clocks = ClockSampler(uuid)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a, b in ev:
+        flush.zero_()
+        a.record(s)
+        g.step(1, w.dt)
+        b.record(s)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    trace = g.trace_read()
+    g.trace(0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ncell = f.ncells
+    value = ncell * world * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel and its roofline
+    peak, peak_kind = measured_peaks()
+    byt = algorithmic_bytes(g, f)
+    dom = max(trace.items(), key=lambda kv: kv[1][0])[0] if trace else None
+    roof = None
+    if dom in byt:
+        avg_ms = trace[dom][0] / trace[dom][1]
+        achieved = byt[dom] / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "bytes_per_launch": byt[dom], "avg_launch_us": round(avg_ms * 1e3, 2),
+                "traffic": recorded_traffic(dom, args.workload)}
+    kernels = {k: {"avg_us": round(v[0] / v[1] * 1e3, 2), "launches": v[1],
+                   "share": round(v[0] / sum(x[0] for x in trace.values()), 3)}
+               for k, v in trace.items()}
+
+    # end to end through the C ABI with host buffers: H2D of m, one step, D2H of m
+    host_in = torch.from_numpy(m0.reshape(-1).copy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ptr_in = host_in.numpy()
+    ptr_out = host_out.numpy()
+    g.set_m(m_dev)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g.set_m_host(ptr_in)
+        g.step(1, w.dt)
+        g.get_m_host(ptr_out)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": ncell * world * args.e2e_steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": 12 * ncell, "d2h_bytes_per_step": 12 * ncell,
+           "steps": args.e2e_steps, "path": "grace_set_m_host + grace_step(1) + grace_get_m_host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+    launches = sum(v[1] for v in trace.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "cells": ncell, "cell_m": list(f.cell), "dt_s": w.dt,
+                   "padded": [int(2 ** math.ceil(math.log2(max(1, 2 * n - 1)))) for n in f.grid],
+                   "initial_state": w.note, "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}", "wall_s_timed_loop": round(wall, 3)},
+        "roofline": roof, "kernels": kernels, "gpu_launches": launches, "e2e": e2e,
+        "cpu_baseline": cpu, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, seconds):
+    """The FP64 oracle as it stands, on the host cores, for a bounded number of steps."""
+    import numpy as np
+
+    from oracle import llg
+    f, m0 = w.films[0], w.m0[0]
+    p = llg.Params(f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, f.hext)
+    nx, ny, nz = f.grid
+    D = llg.Demag((nx, ny, nz), f.cell)          # tensor spectrum: set-up, not timed
+    m = m0.astype(np.float64)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        m = llg.euler_step(m, p, w.dt, D)
+        n += 1
+        if time.perf_counter() - t0 >= seconds or n >= 1000:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": f.ncells * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 Euler steps of the full {w.name} film (numpy FFT convolution, "
+                      f"single thread), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import workloads
+    w = getattr(workloads, args.workload)()
+    budget = max(5.0, min(150.0, args.cpu_seconds * 3))
+    cb = cpu_baseline(w, budget)
+    f = w.films[0]
+    line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f.ncells / cb["value"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "cells": f.ncells, "dt_s": w.dt,
+                       "note": "reference arm = the FP64 CPU oracle; each timed step is one oracle "
+                               "Euler step of the full film, as many as fit the time budget"},
+            "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_grace(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

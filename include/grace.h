@@ -166,13 +166,15 @@ int grace_backward(grace_ctx *ctx, const float *dev_dL_dmT, int n, double dt_s, 
                    float *dev_dL_dms, float *dev_dL_dm0);
 
 /*
- * grace_trace - when on (1), every kernel launched by grace_step / grace_heff /
- * grace_set_m is bracketed by CUDA events on the bound stream (grace_step then uses plain
- * launches instead of graphs).  grace_trace_read synchronises on the last event and
- * returns, per GRACE_KERNEL_* kind, the summed device time in ms and the launch count
- * since the previous read (8 entries each); it then resets them.
+ * grace_trace - capacity > 0 turns per-kernel timing on: the next `capacity` kernels
+ * launched by grace_step / grace_heff / grace_set_m are bracketed by CUDA events on the
+ * bound stream (events are created here, not during the timed work; later launches are
+ * not timed) and grace_step uses plain launches instead of graphs.  0 turns it off.
+ * grace_trace_read synchronises on the last event and returns, per GRACE_KERNEL_* kind,
+ * the summed device time in ms and the number of timed launches since the previous
+ * read (8 entries each); it then resets them and the capacity.
  */
-int grace_trace(grace_ctx *ctx, int on);
+int grace_trace(grace_ctx *ctx, int capacity);
 int grace_trace_read(grace_ctx *ctx, double ms[8], long long counts[8]);
 
 /* grace_set_option - see GRACE_OPT_*. */

@@ -152,14 +152,11 @@ int plan_group(grace_ctx* c, Group& g) {
   }
   if (g.fast) {
     g.fused = true;
-    const int T = g.Q / 8;
-    int TY = c->tile_x > 0 ? c->tile_x : std::min(8, std::max(1, 256 / T));
-    while (TY > 1 && TY * T > 256) TY /= 2;
-    g.TY = TY;
-    g.smem_x = fast_x_smem(g.Q, TY);
-    const int per = 3 * g.nz * (g.Py / 8);
-    int KPB = c->tile_yz > 0 ? c->tile_yz : std::max(1, 256 / per);
-    while (KPB > 1 && KPB * per > 768) --KPB;
+    g.TY = fast_x_tile(g.Q);   // compile-time tile of the fast x pass
+    g.smem_x = fast_x_smem(g.Q, g.TY);
+    const int per = g.nz * (g.Py / 8);
+    int KPB = c->tile_yz > 0 ? c->tile_yz : std::max(1, 128 / per);
+    while (KPB > 1 && KPB * per > 256) --KPB;
     g.KPB = KPB;
     g.smem_yz = fast_yz_smem(g.Py, g.nz, KPB);
     if (g.smem_x > kSmemMax || g.smem_yz > kSmemMax) return GRACE_EUNSUPPORTED;
@@ -413,26 +410,22 @@ const FilmDev* dfilms(const grace_ctx* c) {
   return reinterpret_cast<const FilmDev*>(c->ws + c->o_films);
 }
 
-// Optional per-kernel timing: an event pair around each launch on the launch stream.
+// Optional per-kernel timing: an event pair around each launch on the launch stream,
+// from a pool created by grace_trace (launches beyond its capacity are not timed).
+bool trace_room(const grace_ctx* c) { return c->trace && c->ev_next + 2 <= c->ev.size(); }
+
 cudaError_t mark(grace_ctx* c, int kind, cudaStream_t s) {
-  if (!c->trace) return cudaSuccess;
-  if (c->ev_next == c->ev.size()) {
-    cudaEvent_t e;
-    cudaError_t r = cudaEventCreate(&e);
-    if (r != cudaSuccess) return r;
-    c->ev.push_back(e);
-    c->ev_kind.push_back(kind);
-  }
   c->ev_kind[c->ev_next] = kind;
   return cudaEventRecord(c->ev[c->ev_next++], s);
 }
 
-#define GRACE_LAUNCH(c, kind, s, call)                 \
-  do {                                                 \
-    cudaError_t e_ = mark(c, kind, s);                 \
-    if (e_ == cudaSuccess) e_ = (call);                \
-    if (e_ == cudaSuccess) e_ = mark(c, kind, s);      \
-    if (e_ != cudaSuccess) return e_;                  \
+#define GRACE_LAUNCH(c, kind, s, call)                     \
+  do {                                                     \
+    const bool t_ = trace_room(c);                         \
+    cudaError_t e_ = t_ ? mark(c, kind, s) : cudaSuccess;  \
+    if (e_ == cudaSuccess) e_ = (call);                    \
+    if (e_ == cudaSuccess && t_) e_ = mark(c, kind, s);    \
+    if (e_ != cudaSuccess) return e_;                      \
   } while (0)
 
 cudaError_t enqueue_conv(grace_ctx* c, const Group& g, const LaunchP& lp, cudaStream_t s) {
@@ -881,10 +874,17 @@ int grace_set_option(grace_ctx* c, int option, long long value) {
   }
 }
 
-int grace_trace(grace_ctx* c, int on) {
-  if (!c || (on != 0 && on != 1)) return GRACE_EINVAL;
-  c->trace = on != 0;
+int grace_trace(grace_ctx* c, int capacity) {
+  if (!c || capacity < 0 || capacity > (1 << 22)) return GRACE_EINVAL;
+  c->trace = capacity > 0;
   c->ev_next = 0;
+  const size_t want = 2 * (size_t)capacity;
+  while (c->ev.size() < want) {
+    cudaEvent_t e;
+    GRACE_CUDA(c, cudaEventCreate(&e));
+    c->ev.push_back(e);
+    c->ev_kind.push_back(0);
+  }
   for (int k = 0; k < 8; ++k) {
     c->trace_ms[k] = 0.0;
     c->trace_n[k] = 0;

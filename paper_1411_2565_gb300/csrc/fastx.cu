@@ -16,44 +16,43 @@
 namespace grace {
 namespace {
 
-// Cell update (exchange, anisotropy, Zeeman, Euler + renormalise) for one cell; hs[0..2]
-// hold the demag field on entry (or 0) and Ms m of the cell's new state on exit.
-template <int MODE>
-__device__ __forceinline__ void cell_update(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
-                                            int x, int y, int z, float* hs0, float* hs1, float* hs2) {
+// Per-cell part of H_eff (exchange, anisotropy, Zeeman) added to the demag field in hd;
+// returns m and the total field.  All global loads of a cell happen here, so callers
+// batch several cells' calls before consuming the results.
+struct CellState {
+  float mx, my, mz, Ms, hx, hy, hz;
+};
+
+__device__ __forceinline__ CellState cell_field(const FilmDev& f, unsigned mask, const float* __restrict__ m,
+                                                int i, int x, int y, int z, float hdx, float hdy, float hdz) {
   const int nx = f.nx, ny = f.ny, nz = f.nz, N = f.ncell;
-  const int i = (z * ny + y) * nx + x;
-  const float mx = m[i], my = m[N + i], mz = m[2 * N + i];
-  const float Ms = f.ms_field ? f.ms_field[i] : f.Ms;
-  if (MODE == XM_R2C) {
-    *hs0 = Ms * mx;
-    *hs1 = Ms * my;
-    *hs2 = Ms * mz;
-    return;
-  }
-  const unsigned mask = (MODE == XM_STEP) ? 15u : lp.mask;
-  float hx = *hs0, hy = *hs1, hz = *hs2;
+  CellState c;
+  c.mx = m[i];
+  c.my = m[N + i];
+  c.mz = m[2 * N + i];
+  c.Ms = f.ms_field ? f.ms_field[i] : f.Ms;
+  float hx = hdx, hy = hdy, hz = hdz;
   if (mask & 2u) {
     // six-neighbour Laplacian, sum of (m_j - m_i)/d^2, free boundaries
     float ax = 0.f, ay = 0.f, az = 0.f;
-    if (x > 0) { ax += m[i - 1] - mx; ay += m[N + i - 1] - my; az += m[2 * N + i - 1] - mz; }
-    if (x < nx - 1) { ax += m[i + 1] - mx; ay += m[N + i + 1] - my; az += m[2 * N + i + 1] - mz; }
+    if (x > 0) { ax += m[i - 1] - c.mx; ay += m[N + i - 1] - c.my; az += m[2 * N + i - 1] - c.mz; }
+    if (x < nx - 1) { ax += m[i + 1] - c.mx; ay += m[N + i + 1] - c.my; az += m[2 * N + i + 1] - c.mz; }
     float lx = ax * f.idx2, ly = ay * f.idx2, lz = az * f.idx2;
     ax = ay = az = 0.f;
-    if (y > 0) { ax += m[i - nx] - mx; ay += m[N + i - nx] - my; az += m[2 * N + i - nx] - mz; }
-    if (y < ny - 1) { ax += m[i + nx] - mx; ay += m[N + i + nx] - my; az += m[2 * N + i + nx] - mz; }
+    if (y > 0) { ax += m[i - nx] - c.mx; ay += m[N + i - nx] - c.my; az += m[2 * N + i - nx] - c.mz; }
+    if (y < ny - 1) { ax += m[i + nx] - c.mx; ay += m[N + i + nx] - c.my; az += m[2 * N + i + nx] - c.mz; }
     lx = fmaf(ax, f.idy2, lx); ly = fmaf(ay, f.idy2, ly); lz = fmaf(az, f.idy2, lz);
     const int pl = nx * ny;
     ax = ay = az = 0.f;
-    if (z > 0) { ax += m[i - pl] - mx; ay += m[N + i - pl] - my; az += m[2 * N + i - pl] - mz; }
-    if (z < nz - 1) { ax += m[i + pl] - mx; ay += m[N + i + pl] - my; az += m[2 * N + i + pl] - mz; }
+    if (z > 0) { ax += m[i - pl] - c.mx; ay += m[N + i - pl] - c.my; az += m[2 * N + i - pl] - c.mz; }
+    if (z < nz - 1) { ax += m[i + pl] - c.mx; ay += m[N + i + pl] - c.my; az += m[2 * N + i + pl] - c.mz; }
     lx = fmaf(ax, f.idz2, lx); ly = fmaf(ay, f.idz2, ly); lz = fmaf(az, f.idz2, lz);
-    const float ce = f.cex / Ms;
+    const float ce = f.cex / c.Ms;
     hx = fmaf(ce, lx, hx);
     hy = fmaf(ce, ly, hy);
     hz = fmaf(ce, lz, hz);
   }
-  if (mask & 4u) hx = fmaf(f.can / Ms, mx, hx);
+  if (mask & 4u) hx = fmaf(f.can / c.Ms, c.mx, hx);
   if (mask & 8u) {
     hx += f.hx;
     hy += f.hy;
@@ -64,17 +63,27 @@ __device__ __forceinline__ void cell_update(const FilmDev& f, const LaunchP& lp,
       hz += f.h_field[2 * N + i];
     }
   }
+  c.hx = hx;
+  c.hy = hy;
+  c.hz = hz;
+  return c;
+}
+
+// Writes the cell's result (H for XM_HEFF, m_{n+1} for XM_STEP) and returns Ms m of the
+// state the next spectrum is built from.
+template <int MODE>
+__device__ __forceinline__ float3 cell_apply(const FilmDev& f, const LaunchP& lp, int i, const CellState& c) {
+  const int N = f.ncell;
+  if (MODE == XM_R2C) return make_float3(c.Ms * c.mx, c.Ms * c.my, c.Ms * c.mz);
   if (MODE == XM_HEFF) {
     float* o = lp.out + 3 * f.cell0;
-    o[i] = hx;
-    o[N + i] = hy;
-    o[2 * N + i] = hz;
-    *hs0 = Ms * mx;
-    *hs1 = Ms * my;
-    *hs2 = Ms * mz;
-    return;
+    o[i] = c.hx;
+    o[N + i] = c.hy;
+    o[2 * N + i] = c.hz;
+    return make_float3(c.Ms * c.mx, c.Ms * c.my, c.Ms * c.mz);
   }
   // Eq. 3: dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)], then renormalise
+  const float mx = c.mx, my = c.my, mz = c.mz, hx = c.hx, hy = c.hy, hz = c.hz;
   const float px = my * hz - mz * hy, py = mz * hx - mx * hz, pz = mx * hy - my * hx;
   const float qx = my * pz - mz * py, qy = mz * px - mx * pz, qz = mx * py - my * px;
   const float cdt = f.llg_c * lp.dt;
@@ -89,21 +98,31 @@ __device__ __forceinline__ void cell_update(const FilmDev& f, const LaunchP& lp,
   mo[i] = ux;
   mo[N + i] = uy;
   mo[2 * N + i] = uz;
-  *hs0 = Ms * ux;
-  *hs1 = Ms * uy;
-  *hs2 = Ms * uz;
+  return make_float3(c.Ms * ux, c.Ms * uy, c.Ms * uz);
 }
 
-// Shared memory: TY line buffers (fast_line_stride float2 each) for staging, the
-// Hermitian merge / split and the FFT exchanges, then hs[3][TY][Q] floats holding H_demag
-// per cell and, after the update, Ms m of the new state.
+// Line-buffer stride for TY y lines of 3 components (line (t, c) at (3 t + c) * LS):
+// the staging and store loops run t fastest, so 3 LS must put the TY lines of one k on
+// different bank pairs; the FFT exchanges run j fastest within one line.
+__host__ __device__ constexpr int x_line_stride(int Q, int TY) {
+  return fast_line_stride(Q, TY >= 4 ? 12 : (TY == 2 ? 8 : 0));
+}
+
+// Shared memory: 3 TY line buffers (x_line_stride float2 each) for staging, the Hermitian
+// merge / split and the FFT exchanges, then hs[3][TY][Q] floats holding H_demag per cell
+// and, after the update, Ms m of the new state.
+// y lines per block: 256 threads where the line allows, at most 4 lines
+__host__ __device__ constexpr int x_tile(int Q) {
+  return (256 / (Q / 8)) < 1 ? 1 : ((256 / (Q / 8)) > 4 ? 4 : 256 / (Q / 8));
+}
+
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256, 3) kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+__global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = Q / 8;
   constexpr int TWQ = GRACE_LMAX / (2 * Q);
-  const int NT = blockDim.x;
-  const int TY = NT / T;
-  const int LS = fast_line_stride(Q, T >= 16 ? 16 / TY : T);
+  constexpr int TY = x_tile(Q);
+  constexpr int NT = TY * T;
+  constexpr int LS = x_line_stride(Q, TY);
   const int tid = threadIdx.x;
   const int j = tid % T, ty = tid / T;
   const int unit = blockIdx.x;
@@ -115,97 +134,133 @@ __global__ void __launch_bounds__(256, 3) kx_fast(const FilmDev* __restrict__ fi
   const int y0 = (local - z * nyt) * TY;
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
-  float2* line = sm + ty * LS;
-  float* hs = reinterpret_cast<float*>(sm + TY * LS);          // [3][TY][Q]
+  float2* lines = sm + 3 * ty * LS;                              // this thread's 3 lines
+  float* hs = reinterpret_cast<float*>(sm + 3 * TY * LS);        // [3][TY][Q]
   const float* __restrict__ m = lp.parity ? f.m1 : f.m0;
   const size_t srow = f.srow;
   const size_t sc = (size_t)nz * f.Kx * srow;                    // component stride of S
   float2* Sz = f.S + (size_t)z * f.Kx * srow;                    // S[c=0][z][.][.]
   const bool demag = (MODE == XM_STEP) || (MODE == XM_HEFF && (lp.mask & 1u));
+  const int nst = 3 * (Q + 1) * TY;
 
   if (demag) {
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      const float2* Sc = Sz + c * sc;
-      for (int idx = tid; idx < (Q + 1) * TY; idx += NT) {
-        const int k = idx / TY, t = idx - k * TY;
-        const int yy = y0 + t;
-        sm[t * LS + pad16(k)] = yy < ny ? Sc[(size_t)k * srow + yy] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-      float2 v[8];
+    // staging S -> shared, TY rows contiguous; loads issued in batches of 8 per thread
+    constexpr int U = 8;
+    for (int base = 0; base < nst; base += U * NT) {
+      float2 buf[U];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        // C_k = (X_k + conj X_{Q-k}) + i W^{-k} (X_k - conj X_{Q-k})
-        const int k = j + r * T;
-        const float2 xk = line[pad16(k)], xq = line[pad16(Q - k)];
-        const float2 a = cadd(xk, cconj(xq)), b = csub(xk, cconj(xq));
-        const float2 wb = cmul(cconj(__ldg(lp.tw + k * TWQ)), b);
-        v[r] = make_float2(a.x - wb.y, a.y + wb.x);
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT + tid;
+        const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
+        buf[u] = (idx < nst && y0 + t < ny) ? Sz[c * sc + (size_t)k * srow + y0 + t]
+                                             : make_float2(0.f, 0.f);
       }
-      __syncthreads();
-      fft_reg<Q, +1, false>(v, j, line, lp.tw);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT + tid;
+        const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
+        if (idx < nst) sm[(3 * t + c) * LS + pad16(k)] = buf[u];
+      }
+    }
+    __syncthreads();
+    float2 v[3][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      // C_k = (X_k + conj X_{Q-k}) + i W^{-k} (X_k - conj X_{Q-k})
+      const int k = j + r * T;
+      const float2 w = cconj(__ldg(lp.tw + k * TWQ));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 xk = lines[c * LS + pad16(k)], xq = lines[c * LS + pad16(Q - k)];
+        const float2 a = cadd(xk, cconj(xq)), b = csub(xk, cconj(xq));
+        const float2 wb = cmul(w, b);
+        v[c][r] = make_float2(a.x - wb.y, a.y + wb.x);
+      }
+    }
+    __syncthreads();
+    fft_reg<Q, +1, false, 3>(v, j, lines, LS, lp.tw);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
       float2* h2 = reinterpret_cast<float2*>(hs + (c * TY + ty) * Q);
 #pragma unroll
-      for (int s = 0; s < 4; ++s) h2[j + s * T] = v[s];   // H at cells 2n, 2n+1
+      for (int s = 0; s < 4; ++s) h2[j + s * T] = v[c][s];     // H at cells 2n, 2n+1
     }
   } else {
     for (int idx = tid; idx < 3 * TY * Q; idx += NT) hs[idx] = 0.f;
   }
   __syncthreads();
 
-  // cell update, one thread per cell of the TY x Q tile (x >= nx, y >= ny give zeros)
-  for (int idx = tid; idx < TY * Q; idx += NT) {
-    const int t = idx / Q, x = idx - t * Q, y = y0 + t;
-    float* h0 = hs + (0 * TY + t) * Q + x;
-    float* h1 = hs + (1 * TY + t) * Q + x;
-    float* h2 = hs + (2 * TY + t) * Q + x;
-    if (x < nx && y < ny) {
-      cell_update<MODE>(f, lp, m, x, y, z, h0, h1, h2);
-    } else {
-      *h0 = 0.f;
-      *h1 = 0.f;
-      *h2 = 0.f;
+  // cell update, one thread per cell of the TY x Q tile (x >= nx, y >= ny give zeros);
+  // each thread owns 8 cells and issues the loads of 4 of them before using any
+  {
+    const unsigned mask = (MODE == XM_STEP) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
+    constexpr int U = 4;
+    for (int base = 0; base < TY * Q; base += U * NT) {
+      CellState cs[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT + tid;
+        const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+        ok[u] = idx < TY * Q && x < nx && y < ny;
+        if (ok[u]) {
+          const float* hp = hs + t * Q + x;
+          cs[u] = cell_field(f, mask, m, (z * ny + y) * nx + x, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT + tid;
+        if (idx >= TY * Q) continue;
+        const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+        float3 r = make_float3(0.f, 0.f, 0.f);
+        if (ok[u]) r = cell_apply<MODE>(f, lp, (z * ny + y) * nx + x, cs[u]);
+        float* hp = hs + t * Q + x;
+        hp[0] = r.x;
+        hp[TY * Q] = r.y;
+        hp[2 * TY * Q] = r.z;
+      }
     }
   }
   const bool r2c = (MODE != XM_HEFF) || demag;
   if (!r2c) return;
   __syncthreads();
-#pragma unroll 1
-  for (int c = 0; c < 3; ++c) {
-    float2 v[8];
-    const float2* h2 = reinterpret_cast<const float2*>(hs + (c * TY + ty) * Q);
+  {
+    float2 v[3][8];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      v[s] = h2[j + s * T];
-      v[s + 4] = make_float2(0.f, 0.f);
+    for (int c = 0; c < 3; ++c) {
+      const float2* h2 = reinterpret_cast<const float2*>(hs + (c * TY + ty) * Q);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        v[c][s] = h2[j + s * T];
+        v[c][s + 4] = make_float2(0.f, 0.f);
+      }
     }
-    fft_reg<Q, -1, true>(v, j, line, lp.tw);
+    fft_reg<Q, -1, true, 3>(v, j, lines, LS, lp.tw);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) line[pad16(j + r * T)] = v[r];
-    __syncthreads();
-    float2 xo[8];
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      // X_k = (Z_k + conj Z_{Q-k})/2 - (i/2) W^k (Z_k - conj Z_{Q-k})
-      const int k = j + r * T;
-      const float2 zq = line[pad16((Q - k) & (Q - 1))];
-      const float2 a = cadd(v[r], cconj(zq)), b = csub(v[r], cconj(zq));
+      for (int r = 0; r < 8; ++r) lines[c * LS + pad16(j + r * T)] = v[c][r];
+  }
+  __syncthreads();
+  // split and store, TY rows of S contiguous:
+  // X_k = (Z_k + conj Z_{Q-k})/2 - (i/2) W^k (Z_k - conj Z_{Q-k}), X_Q = Re Z_0 - Im Z_0
+  for (int idx = tid; idx < nst; idx += NT) {
+    const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
+    const int yy = y0 + t;
+    if (yy >= ny) continue;
+    const float2* ln = sm + (3 * t + c) * LS;
+    const float2 zk = ln[pad16(k & (Q - 1))];
+    float2 xo;
+    if (k == Q) {
+      xo = make_float2(zk.x - zk.y, 0.f);
+    } else {
+      const float2 zq = ln[pad16((Q - k) & (Q - 1))];
+      const float2 a = cadd(zk, cconj(zq)), b = csub(zk, cconj(zq));
       const float2 wb = cmul(__ldg(lp.tw + k * TWQ), b);
-      xo[r] = make_float2(0.5f * (a.x + wb.y), 0.5f * (a.y - wb.x));
+      xo = make_float2(0.5f * (a.x + wb.y), 0.5f * (a.y - wb.x));
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 8; ++r) line[pad16(j + r * T)] = xo[r];
-    if (j == 0) line[pad16(Q)] = make_float2(v[0].x - v[0].y, 0.f);
-    __syncthreads();
-    float2* Sc = Sz + c * sc;
-    for (int idx = tid; idx < (Q + 1) * TY; idx += NT) {
-      const int k = idx / TY, t = idx - k * TY;
-      const int yy = y0 + t;
-      if (yy < ny) Sc[(size_t)k * srow + yy] = sm[t * LS + pad16(k)];
-    }
-    __syncthreads();
+    Sz[c * sc + (size_t)k * srow + yy] = xo;
   }
 }
 
@@ -233,10 +288,10 @@ cudaError_t attr_q(size_t smem) {
 
 bool fast_x_supported(int Q) { return Q >= 8 && Q <= 2048; }
 
+int fast_x_tile(int Q) { return x_tile(Q); }
+
 size_t fast_x_smem(int Q, int TY) {
-  const int T = Q / 8;
-  const int LS = fast_line_stride(Q, T >= 16 ? 16 / TY : T);
-  return (size_t)TY * LS * sizeof(float2) + (size_t)3 * TY * Q * sizeof(float);
+  return (size_t)3 * TY * x_line_stride(Q, TY) * sizeof(float2) + (size_t)3 * TY * Q * sizeof(float);
 }
 
 cudaError_t configure_fast_x(int Q, size_t smem) {

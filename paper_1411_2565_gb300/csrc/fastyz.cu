@@ -57,16 +57,16 @@ __device__ __forceinline__ void tensor_product(const float* __restrict__ Tk, int
 }
 
 template <int PY, int NZ>
-__global__ void __launch_bounds__(768) kyz_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+__global__ void __launch_bounds__(256, 3) kyz_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = PY / 8;
   constexpr int NL = 3 * NZ;
   constexpr int LS = fast_line_stride(PY, T);
-  const int KPB = blockDim.x / (NL * T);
+  const int KPB = blockDim.x / (NZ * T);
   const int tid = threadIdx.x;
   const int j = tid % T;
-  const int li = tid / T;             // kxi * NL + line
-  const int line = li % NL;
-  const int kxi = li / NL;
+  const int gi = tid / T;              // kxi * NZ + z
+  const int z = gi % NZ;
+  const int kxi = gi / NZ;
   const int unit = blockIdx.x;
   const FilmDev& f = films[find_film(films, lp.nfilms, UK_YZ, unit)];
   const int kx0 = (unit - f.u0[UK_YZ]) * KPB;
@@ -75,19 +75,25 @@ __global__ void __launch_bounds__(768) kyz_fast(const FilmDev* __restrict__ film
   const int ny = f.ny;
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
-  float2* buf = sm + li * LS;
-  float2* S = f.S + ((size_t)line * f.Kx + kx) * f.srow;
+  float2* lines = sm + (kxi * NL + z) * LS;            // lines (c, z), c = 0..2, NZ*LS apart
+  const size_t cs = (size_t)NZ * f.Kx * f.srow;        // component stride of S
+  const float2* S0 = f.S + ((size_t)z * f.Kx + (ok ? kx : 0)) * f.srow;
 
-  float2 v[8];
+  float2 v[3][8];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int y = j + r * T;
-    v[r] = (ok && y < ny) ? S[y] : make_float2(0.f, 0.f);
-    v[r + 4] = make_float2(0.f, 0.f);
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int y = j + r * T;
+      v[c][r] = (ok && y < ny) ? S0[c * cs + y] : make_float2(0.f, 0.f);
+      v[c][r + 4] = make_float2(0.f, 0.f);
+    }
   }
-  fft_reg<PY, -1, true>(v, j, buf, lp.tw);
+  fft_reg<PY, -1, true, 3>(v, j, lines, NZ * LS, lp.tw);
 #pragma unroll
-  for (int r = 0; r < 8; ++r) buf[pad16(j + r * T)] = v[r];
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) lines[c * NZ * LS + pad16(j + r * T)] = v[c][r];
   __syncthreads();
 
   const int npair = KPB * PY;
@@ -103,28 +109,34 @@ __global__ void __launch_bounds__(768) kyz_fast(const FilmDev* __restrict__ film
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int z = 0; z < NZ; ++z) M[c][z] = base[(c * NZ + z) * LS];
+      for (int zz = 0; zz < NZ; ++zz) M[c][zz] = base[(c * NZ + zz) * LS];
     tensor_product<NZ>(f.T + (size_t)kxx * f.nslot * f.Ky + kyp, f.Ky, sy, M, H);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int z = 0; z < NZ; ++z) base[(c * NZ + z) * LS] = H[c][z];
+      for (int zz = 0; zz < NZ; ++zz) base[(c * NZ + zz) * LS] = H[c][zz];
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < 8; ++r) v[r] = buf[pad16(j + r * T)];
-  __syncthreads();
-  fft_reg<PY, +1, false>(v, j, buf, lp.tw);
+  for (int c = 0; c < 3; ++c)
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int y = j + r * T;
-    if (ok && y < ny) S[y] = v[r];
-  }
+    for (int r = 0; r < 8; ++r) v[c][r] = lines[c * NZ * LS + pad16(j + r * T)];
+  __syncthreads();
+  fft_reg<PY, +1, false, 3>(v, j, lines, NZ * LS, lp.tw);
+  if (!ok) return;
+  float2* S1 = f.S + ((size_t)z * f.Kx + kx) * f.srow;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int y = j + r * T;
+      if (y < ny) S1[c * cs + y] = v[c][r];
+    }
 }
 
 template <int PY, int NZ>
 constexpr bool yz_ok() {
-  return 3 * NZ * (PY / 8) <= 768;
+  return NZ * (PY / 8) <= 256;
 }
 
 template <int PY, int NZ>
@@ -172,7 +184,7 @@ cudaError_t dispatch(int Py, int nz, const FilmDev* films, const LaunchP& lp, in
 }  // namespace
 
 bool fast_yz_supported(int Py, int nz) {
-  return Py >= 8 && Py <= 2048 && nz >= 1 && nz <= 4 && 3 * nz * (Py / 8) <= 768;
+  return Py >= 8 && Py <= 2048 && nz >= 1 && nz <= 4 && nz * (Py / 8) <= 256;
 }
 
 size_t fast_yz_smem(int Py, int nz, int kpb) {
@@ -187,7 +199,7 @@ cudaError_t configure_fast_yz(int Py, int nz, size_t smem) {
 cudaError_t launch_fast_yz(int Py, int nz, const FilmDev* films, const LaunchP& lp, int nunits, int kpb,
                            size_t smem, cudaStream_t s) {
   if (nunits <= 0) return cudaSuccess;
-  const int threads = kpb * 3 * nz * (Py / 8);
+  const int threads = kpb * nz * (Py / 8);
   return dispatch(Py, nz, films, lp, nunits, threads, smem, s, false);
 }
 

@@ -60,24 +60,10 @@ __device__ __forceinline__ void dft8_upper_zero(float2* v) {
   v[7] = csub(e3, t3);
 }
 
-// v[r] *= w^r for r = 1..7, w = table[m]: three table loads (w, w^2, w^4), four products.
-template <int DIR>
-__device__ __forceinline__ void twiddle8(float2 (&v)[8], const float2* __restrict__ tw, int m) {
-  const float2 w1 = twiddle<DIR>(tw, m);
-  const float2 w2 = twiddle<DIR>(tw, 2 * m);
-  const float2 w4 = twiddle<DIR>(tw, 4 * m);
-  const float2 w3 = cmul(w1, w2);
-  v[1] = cmul(v[1], w1);
-  v[2] = cmul(v[2], w2);
-  v[3] = cmul(v[3], w3);
-  v[4] = cmul(v[4], w4);
-  v[5] = cmul(v[5], cmul(w1, w4));
-  v[6] = cmul(v[6], cmul(w2, w4));
-  v[7] = cmul(v[7], cmul(w3, w4));
-}
-
-template <int L, int NS, int DIR, bool FIRST, bool ZU>
-__device__ __forceinline__ void fft_reg_stage(float2 (&v)[8], int j, float2* sm,
+// G lines per thread: v[g][s] = x_g[j + s L/8]; line g's buffer starts at sm + g * gs.
+// The twiddles depend only on (j, stage) and are shared by the G lines.
+template <int L, int NS, int DIR, bool FIRST, bool ZU, int G>
+__device__ __forceinline__ void fft_reg_stage(float2 (&v)[G][8], int j, float2* sm, int gs,
                                               const float2* __restrict__ tw) {
   constexpr int L8 = L / 8;
   constexpr int REM = L / NS;
@@ -86,55 +72,86 @@ __device__ __forceinline__ void fft_reg_stage(float2 (&v)[8], int j, float2* sm,
   constexpr int TWS = GRACE_LMAX / (NS * R);
   if constexpr (R == 8) {
     const int k = j & (NS - 1);
-    if constexpr (NS > 1) twiddle8<DIR>(v, tw, k * TWS);
-    if constexpr (FIRST && ZU) dft8_upper_zero<DIR>(v);
-    else dft8<DIR>(v);
+    if constexpr (NS > 1) {
+      const int m = k * TWS;
+      const float2 w1 = twiddle<DIR>(tw, m), w2 = twiddle<DIR>(tw, 2 * m), w4 = twiddle<DIR>(tw, 4 * m);
+      const float2 w3 = cmul(w1, w2);
+      const float2 w[8] = {w1, w1, w2, w3, w4, cmul(w1, w4), cmul(w2, w4), cmul(w3, w4)};
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v[g][r] = cmul(v[g][r], w[r]);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if constexpr (FIRST && ZU) dft8_upper_zero<DIR>(v[g]);
+      else dft8<DIR>(v[g]);
+    }
     if constexpr (!LAST) {
       const int o = (j - k) * 8 + k;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) sm[padx<NS>(o + r * NS)] = v[r];
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sm[g * gs + padx<NS>(o + r * NS)] = v[g][r];
       __syncthreads();
 #pragma unroll
-      for (int s = 0; s < 8; ++s) v[s] = sm[padx<NS>(j + s * L8)];
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[g][s] = sm[g * gs + padx<NS>(j + s * L8)];
       __syncthreads();
-      fft_reg_stage<L, NS * 8, DIR, false, ZU>(v, j, sm, tw);
+      fft_reg_stage<L, NS * 8, DIR, false, ZU, G>(v, j, sm, gs, tw);
     }
   } else if constexpr (R == 4) {
     // last stage (NS = L/4): butterflies jj = j + b L/8 on v[2r + b]; outputs return in place
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       const int k = j + b * L8;
-      float2 a0 = v[b], a1 = v[2 + b], a2 = v[4 + b], a3 = v[6 + b];
+      float2 w1 = make_float2(1.f, 0.f), w2 = w1, w3 = w1;
       if constexpr (NS > 1) {
-        const float2 w1 = twiddle<DIR>(tw, k * TWS), w2 = twiddle<DIR>(tw, 2 * k * TWS);
-        a1 = cmul(a1, w1);
-        a2 = cmul(a2, w2);
-        a3 = cmul(a3, cmul(w1, w2));
+        w1 = twiddle<DIR>(tw, k * TWS);
+        w2 = twiddle<DIR>(tw, 2 * k * TWS);
+        w3 = cmul(w1, w2);
       }
-      dft4<DIR>(a0, a1, a2, a3);
-      v[b] = a0;
-      v[2 + b] = a1;
-      v[4 + b] = a2;
-      v[6 + b] = a3;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        float2 a0 = v[g][b], a1 = v[g][2 + b], a2 = v[g][4 + b], a3 = v[g][6 + b];
+        if constexpr (NS > 1) {
+          a1 = cmul(a1, w1);
+          a2 = cmul(a2, w2);
+          a3 = cmul(a3, w3);
+        }
+        dft4<DIR>(a0, a1, a2, a3);
+        v[g][b] = a0;
+        v[g][2 + b] = a1;
+        v[g][4 + b] = a2;
+        v[g][6 + b] = a3;
+      }
     }
   } else {
     // last stage (NS = L/2): butterflies jj = j + b L/8 on (v[b], v[b + 4])
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int k = j + b * L8;
-      float2 a0 = v[b], a1 = v[b + 4];
-      if constexpr (NS > 1) a1 = cmul(a1, twiddle<DIR>(tw, k * TWS));
-      dft2<DIR>(a0, a1);
-      v[b] = a0;
-      v[b + 4] = a1;
+      float2 w1 = make_float2(1.f, 0.f);
+      if constexpr (NS > 1) w1 = twiddle<DIR>(tw, k * TWS);
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        float2 a0 = v[g][b], a1 = v[g][b + 4];
+        if constexpr (NS > 1) a1 = cmul(a1, w1);
+        dft2<DIR>(a0, a1);
+        v[g][b] = a0;
+        v[g][b + 4] = a1;
+      }
     }
   }
 }
 
-template <int L, int DIR, bool ZU>
-__device__ __forceinline__ void fft_reg(float2 (&v)[8], int j, float2* sm, const float2* __restrict__ tw) {
+// In-place transform of G lines held by the calling thread (see the file comment).
+template <int L, int DIR, bool ZU, int G>
+__device__ __forceinline__ void fft_reg(float2 (&v)[G][8], int j, float2* sm, int gs,
+                                        const float2* __restrict__ tw) {
   static_assert(L >= 8 && (L & (L - 1)) == 0 && L <= GRACE_LMAX, "power-of-two length 8..LMAX");
-  fft_reg_stage<L, 1, DIR, true, ZU>(v, j, sm, tw);
+  fft_reg_stage<L, 1, DIR, true, ZU, G>(v, j, sm, gs, tw);
 }
 
 }  // namespace grace

@@ -32,9 +32,11 @@ def _dev_ptr(t: torch.Tensor, numel: int, what: str) -> int:
 
 
 class _Base:
-    def _init(self, ctx: C.c_void_p, device, stream):
+    def _init(self, ctx: C.c_void_p, device, stream, options=None):
         self._L = _lib.load()
         self.ctx = ctx
+        for opt, val in (options or {}).items():      # tile options must precede the bind
+            check(self._L.grace_set_option(ctx, int(opt), int(val)), "grace_set_option", ctx)
         self.device = torch.device(device)
         n = C.c_longlong()
         check(self._L.grace_ncells(ctx, C.byref(n)), "grace_ncells", ctx)
@@ -87,8 +89,9 @@ class _Base:
         check(self._L.grace_set_ms_field(self.ctx, ptr), "grace_set_ms_field", self.ctx)
         self._keep["ms"] = ms
 
-    def trace(self, on: bool = True):
-        check(self._L.grace_trace(self.ctx, 1 if on else 0), "grace_trace", self.ctx)
+    def trace(self, capacity: int = 1 << 16):
+        """Time the next ``capacity`` kernel launches with CUDA events (0 switches it off)."""
+        check(self._L.grace_trace(self.ctx, int(capacity)), "grace_trace", self.ctx)
 
     def trace_read(self):
         """{kernel kind: (total ms, launches)} since the last read (see GRACE_KERNEL_*)."""
@@ -134,13 +137,13 @@ class Grace(_Base):
     """One rectangular film (grid (nx, ny, nz), cell (dx, dy, dz) in metres)."""
 
     def __init__(self, grid, cell, Ms, A, Ku=0.0, alpha=0.1, gamma0=GAMMA0, device="cuda",
-                 stream: Optional[torch.cuda.Stream] = None):
+                 stream: Optional[torch.cuda.Stream] = None, options=None):
         L = _lib.load()
         ctx = C.c_void_p()
         check(L.grace_create(C.byref(ctx), ivec(grid), dvec(cell), float(Ms), float(A), float(Ku),
                              float(alpha), float(gamma0)), "grace_create")
         self.grid = tuple(int(g) for g in grid)
-        self._init(ctx, device, stream)
+        self._init(ctx, device, stream, options)
 
     @property
     def shape(self):
@@ -151,7 +154,7 @@ class Grace(_Base):
 class GraceBatch(_Base):
     """Independent films stepped together; arrays are the films concatenated in order."""
 
-    def __init__(self, films, device="cuda", stream: Optional[torch.cuda.Stream] = None):
+    def __init__(self, films, device="cuda", stream: Optional[torch.cuda.Stream] = None, options=None):
         L = _lib.load()
         ctx = C.c_void_p()
         n = len(films)
@@ -162,7 +165,7 @@ class GraceBatch(_Base):
                                    dvec([f.Ku for f in films]), dvec([f.alpha for f in films]),
                                    dvec([f.gamma0 for f in films])), "grace_batch_create")
         self.films = list(films)
-        self._init(ctx, device, stream)
+        self._init(ctx, device, stream, options)
         for i, f in enumerate(films):
             check(L.grace_set_film_hext(ctx, i, dvec(f.hext)), "grace_set_film_hext", ctx)
         self.offsets = np.cumsum([0] + [3 * f.ncells for f in films])
