@@ -177,6 +177,36 @@ int grace_backward(grace_ctx *ctx, const float *dev_dL_dmT, int n, double dt_s, 
 int grace_trace(grace_ctx *ctx, int capacity);
 int grace_trace_read(grace_ctx *ctx, double ms[8], long long counts[8]);
 
+/*
+ * grace_energy_noalloc - the energies of grace_energy for callers that cannot allocate
+ * device memory.  No counterpart in the paper: it serves hosts that hold the state but
+ * may not allocate on the device, e.g. a monitoring hook inside another framework's step
+ * (that framework's caching allocator owns the device pool, where a raw allocation can
+ * fail or fragment it), or a real-time loop whose policy forbids allocation after
+ * start-up.  Needs no handle and no workspace; allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library call).
+ *   grid, cell_m, Ms, A, Ku, hext : the film, as for grace_create / grace_set_hext
+ *                                   (uniform Ms and field).
+ *   dev_m       device, 3*N floats, the state [3][nz][ny][nx].
+ *   dev_hdemag  device, 3*N floats, its demag field (e.g. from grace_heff with
+ *               GRACE_TERM_DEMAG).
+ *   cuda_stream the stream the work is queued on; the call synchronises it.
+ *   out[5], mavg[3] as for grace_energy (either may be NULL).
+ * Scratch: per-block FP64 partial sums in one file-scope device array of
+ * GRACE_ENERGY_NOALLOC_MAX_CELLS / 4096 * 64 bytes (256 KiB), reserved by every GPU
+ * that loads the library until the process exits.  N above GRACE_ENERGY_NOALLOC_MAX_CELLS
+ * returns GRACE_EUNSUPPORTED.  The first call on a device looks up that array's device
+ * address (with the device current), so make it before any stream capture.  All calls
+ * share the array; each call rewrites every slot it reads, so no clearing is needed, but
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * Returns GRACE_EINVAL for bad arguments, GRACE_ECUDA on a CUDA failure,
+ * GRACE_ENONFINITE if <m> is not finite.
+ */
+#define GRACE_ENERGY_NOALLOC_MAX_CELLS (16 * 1024 * 1024)
+int grace_energy_noalloc(const int grid[3], const double cell_m[3], double Ms, double A, double Ku,
+                         const double hext[3], const float *dev_m, const float *dev_hdemag,
+                         void *cuda_stream, double out[5], double mavg[3]);
+
 /* grace_set_option - see GRACE_OPT_*. */
 int grace_set_option(grace_ctx *ctx, int option, long long value);
 

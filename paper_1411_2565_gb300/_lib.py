@@ -44,6 +44,7 @@ SIGNATURES = {
     "grace_set_option": (_I, [_P, _I, C.c_longlong]),
     "grace_trace": (_I, [_P, _I]),
     "grace_trace_read": (_I, [_P, _DP, C.POINTER(C.c_longlong)]),
+    "grace_energy_noalloc": (_I, [_IP, _DP, _D, _D, _D, _DP, _P, _P, _P, _DP, _DP]),
     "grace_last_error": (C.c_char_p, [_P]),
     "grace_destroy": (_I, [_P]),
 }
