@@ -825,18 +825,112 @@ int grace_energy(grace_ctx* c, double out[5], double mavg[3]) {
   return GRACE_OK;
 }
 
-int grace_backward_workspace_size(const grace_ctx* c, int n, int ckpt_every, size_t* bytes) {
-  if (!c || !bytes || n < 0 || ckpt_every < 1) return GRACE_EINVAL;
-  *bytes = 0;
-  return fail(const_cast<grace_ctx*>(c), GRACE_EUNSUPPORTED, "backward not built");
+namespace {
+
+size_t adj_state_bytes(const grace_ctx* c) { return al256((size_t)3 * c->ncell * sizeof(float)); }
+
+int adj_checkpoints(int n, int ckpt) { return n > 0 ? (n + ckpt - 1) / ckpt : 1; }
+
+float* cur_m(grace_ctx* c) {
+  return reinterpret_cast<float*>(c->ws + c->o_run + (c->parity ? c->o_m1 : c->o_m0));
 }
 
-int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt_every, void* scratch,
-                   size_t scratch_bytes, float* dL_dhext, float* dL_dms, float* dL_dm0) {
-  (void)dL_dmT; (void)n; (void)dt; (void)ckpt_every; (void)scratch; (void)scratch_bytes;
-  (void)dL_dhext; (void)dL_dms; (void)dL_dm0;
-  if (!c) return GRACE_EINVAL;
-  return fail(c, GRACE_EUNSUPPORTED, "backward not built");
+int copy_state(grace_ctx* c, float* dst, const float* src) {
+  GRACE_CUDA(c, cudaMemcpyAsync(dst, src, (size_t)3 * c->ncell * sizeof(float), cudaMemcpyDeviceToDevice,
+                                c->stream));
+  return GRACE_OK;
+}
+
+}  // namespace
+
+int grace_backward_workspace_size(const grace_ctx* c, int n, int ckpt_every, size_t* bytes) {
+  if (!c || !bytes || n < 0 || ckpt_every < 1) return GRACE_EINVAL;
+  const size_t seg = (size_t)std::min(ckpt_every, std::max(n, 1));
+  *bytes = (adj_checkpoints(n, ckpt_every) + seg + 4) * adj_state_bytes(c);
+  return GRACE_OK;
+}
+
+// Discrete adjoint of n Euler steps (see grace.h).  Memory: one state per checkpoint plus
+// one segment of ckpt_every states, recomputed forward from its checkpoint.  Per backward
+// step k: R2C of Ms m_k, y pass, ADJ1 (H_eff(m_k), normalisation and LLG Jacobians,
+// R2C of nu), y pass, ADJ2 (demag of nu, exchange adjoint, lambda_k).
+int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt, void* scratch,
+                   size_t scratch_bytes, float* g_hext, float* g_ms, float* g_m0) {
+  int st = ready(c, true);
+  if (st) return st;
+  if (!dL_dmT) return fail(c, GRACE_EINVAL, "dL/dm_T pointer is NULL");
+  if (n < 0 || ckpt < 1) return fail(c, GRACE_EINVAL, "n must be >= 0 and ckpt_every >= 1");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GRACE_EINVAL, "dt must be positive");
+  size_t need = 0;
+  grace_backward_workspace_size(c, n, ckpt, &need);
+  if (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 255u) || scratch_bytes < need)
+    return fail(c, GRACE_EWORKSPACE, "backward scratch missing, misaligned or smaller than "
+                                     "grace_backward_workspace_size");
+  const float fdt = (float)dt;
+  const size_t sb = adj_state_bytes(c);
+  const int nck = adj_checkpoints(n, ckpt);
+  const int segn = std::min(ckpt, std::max(n, 1));
+  char* base = static_cast<char*>(scratch);
+  auto state = [&](int k) { return reinterpret_cast<float*>(base + (size_t)k * sb); };
+  float* ck0 = state(0);
+  float* seg0 = state(nck);
+  float* lamA = state(nck + segn);
+  float* lamB = state(nck + segn + 1);
+  float* lampart = state(nck + segn + 2);
+  float* nu = state(nck + segn + 3);
+  const bool saved_trace = c->trace;
+  c->trace = false;
+
+  // forward from m_0, keeping the state at every checkpoint
+  if ((st = copy_state(c, ck0, cur_m(c)))) return st;
+  for (int s = 1; s < nck; ++s) {
+    for (int k = 0; k < ckpt; ++k) {
+      GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, c->stream));
+      c->parity ^= 1;
+    }
+    if ((st = copy_state(c, state(s), cur_m(c)))) return st;
+  }
+  if ((st = copy_state(c, lamA, dL_dmT))) return st;
+  for (int s = nck - 1; s >= 0 && n > 0; --s) {
+    const int k0 = s * ckpt;
+    const int len = std::min(ckpt, n - k0);
+    // recompute the segment's states m_{k0} .. m_{k0+len-1}
+    if ((st = copy_state(c, cur_m(c), state(s)))) return st;
+    GRACE_CUDA(c, enqueue_r2c(c));
+    for (int j = 0; j < len; ++j) {
+      if ((st = copy_state(c, seg0 + (size_t)j * (sb / sizeof(float)), cur_m(c)))) return st;
+      if (j + 1 < len) {
+        GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, c->stream));
+        c->parity ^= 1;
+      }
+    }
+    for (int j = len - 1; j >= 0; --j) {
+      const float* mk = seg0 + (size_t)j * (sb / sizeof(float));
+      for (const auto& g : c->groups) {
+        LaunchP lp = group_lp(c, g);
+        lp.dt = fdt;
+        lp.mk = mk;
+        lp.adj_lam_in = lamA;
+        lp.adj_lam_part = lampart;
+        lp.adj_nu = nu;
+        lp.adj_lam_out = lamB;
+        lp.adj_g_hext = g_hext;
+        lp.adj_g_ms = g_ms;
+        GRACE_CUDA(c, enqueue_x(c, g, XM_R2C, lp, c->stream));
+        GRACE_CUDA(c, enqueue_conv(c, g, lp, c->stream));
+        GRACE_CUDA(c, enqueue_x(c, g, XM_ADJ1, lp, c->stream));
+        GRACE_CUDA(c, enqueue_conv(c, g, lp, c->stream));
+        GRACE_CUDA(c, enqueue_x(c, g, XM_ADJ2, lp, c->stream));
+      }
+      std::swap(lamA, lamB);
+    }
+  }
+  if (g_m0 && (st = copy_state(c, g_m0, lamA))) return st;
+  // leave the state at m_0
+  if ((st = copy_state(c, cur_m(c), ck0))) return st;
+  GRACE_CUDA(c, enqueue_r2c(c));
+  c->trace = saved_trace;
+  return GRACE_OK;
 }
 
 int grace_set_option(grace_ctx* c, int option, long long value) {

@@ -1,0 +1,196 @@
+// Per-cell parts of the x pass, shared by the fast and the runtime-length kernels:
+// the local terms of H_eff (Eq. 2), the explicit Euler step of Eq. 3 with
+// renormalisation, and the two pointwise halves of its discrete adjoint.
+#pragma once
+#include "internal.cuh"
+
+namespace grace {
+
+struct CellState {
+  float mx, my, mz, Ms, hx, hy, hz;
+};
+
+__device__ __forceinline__ float cell_ms(const FilmDev& f, int i) { return f.ms_field ? f.ms_field[i] : f.Ms; }
+
+// Six-neighbour Laplacian of the vector field a (component stride N) at cell i, with
+// per-cell weights w (w == nullptr: weight 1): sum_d sum_j (w_j a_j - w_i a_i)/d^2,
+// free boundaries.  Differences are formed before the 1/d^2 scaling.
+template <bool WEIGHTED>
+__device__ __forceinline__ float3 laplacian(const FilmDev& f, const float* __restrict__ a, int i, int x,
+                                            int y, int z, float wi, float cw) {
+  const int nx = f.nx, ny = f.ny, nz = f.nz, N = f.ncell;
+  auto w = [&](int j) { return WEIGHTED ? cw / cell_ms(f, j) : 1.f; };
+  const float ax0 = wi * a[i], ay0 = wi * a[N + i], az0 = wi * a[2 * N + i];
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  float bx = 0.f, by = 0.f, bz = 0.f;
+  if (x > 0) { const float wj = w(i - 1); bx += wj * a[i - 1] - ax0; by += wj * a[N + i - 1] - ay0; bz += wj * a[2 * N + i - 1] - az0; }
+  if (x < nx - 1) { const float wj = w(i + 1); bx += wj * a[i + 1] - ax0; by += wj * a[N + i + 1] - ay0; bz += wj * a[2 * N + i + 1] - az0; }
+  sx = bx * f.idx2; sy = by * f.idx2; sz = bz * f.idx2;
+  bx = by = bz = 0.f;
+  if (y > 0) { const int j = i - nx; const float wj = w(j); bx += wj * a[j] - ax0; by += wj * a[N + j] - ay0; bz += wj * a[2 * N + j] - az0; }
+  if (y < ny - 1) { const int j = i + nx; const float wj = w(j); bx += wj * a[j] - ax0; by += wj * a[N + j] - ay0; bz += wj * a[2 * N + j] - az0; }
+  sx = fmaf(bx, f.idy2, sx); sy = fmaf(by, f.idy2, sy); sz = fmaf(bz, f.idy2, sz);
+  bx = by = bz = 0.f;
+  const int pl = nx * ny;
+  if (z > 0) { const int j = i - pl; const float wj = w(j); bx += wj * a[j] - ax0; by += wj * a[N + j] - ay0; bz += wj * a[2 * N + j] - az0; }
+  if (z < nz - 1) { const int j = i + pl; const float wj = w(j); bx += wj * a[j] - ax0; by += wj * a[N + j] - ay0; bz += wj * a[2 * N + j] - az0; }
+  sx = fmaf(bx, f.idz2, sx); sy = fmaf(by, f.idz2, sy); sz = fmaf(bz, f.idz2, sz);
+  return make_float3(sx, sy, sz);
+}
+
+// m at cell i and its H_eff restricted to `mask` with hd as the demag part.  All global
+// loads of a cell happen here, so callers batch several cells' calls before using them.
+__device__ __forceinline__ CellState cell_field(const FilmDev& f, unsigned mask, const float* __restrict__ m,
+                                                int i, int x, int y, int z, float hdx, float hdy, float hdz) {
+  const int N = f.ncell;
+  CellState c;
+  c.mx = m[i];
+  c.my = m[N + i];
+  c.mz = m[2 * N + i];
+  c.Ms = cell_ms(f, i);
+  float hx = hdx, hy = hdy, hz = hdz;
+  if (mask & 2u) {
+    const float3 l = laplacian<false>(f, m, i, x, y, z, 1.f, 0.f);
+    const float ce = f.cex / c.Ms;          // 2A/(mu0 Ms), observer cell
+    hx = fmaf(ce, l.x, hx);
+    hy = fmaf(ce, l.y, hy);
+    hz = fmaf(ce, l.z, hz);
+  }
+  if (mask & 4u) hx = fmaf(f.can / c.Ms, c.mx, hx);
+  if (mask & 8u) {
+    hx += f.hx;
+    hy += f.hy;
+    hz += f.hz;
+    if (f.h_field) {
+      hx += f.h_field[i];
+      hy += f.h_field[N + i];
+      hz += f.h_field[2 * N + i];
+    }
+  }
+  c.hx = hx;
+  c.hy = hy;
+  c.hz = hz;
+  return c;
+}
+
+__device__ __forceinline__ float3 cross3(float ax, float ay, float az, float bx, float by, float bz) {
+  return make_float3(ay * bz - az * by, az * bx - ax * bz, ax * by - ay * bx);
+}
+
+// Writes the cell's result (H for XM_HEFF, m_{n+1} for XM_STEP) and returns Ms m of the
+// state the next spectrum is built from.
+template <int MODE>
+__device__ __forceinline__ float3 cell_apply(const FilmDev& f, const LaunchP& lp, int i, const CellState& c) {
+  const int N = f.ncell;
+  if (MODE == XM_R2C) return make_float3(c.Ms * c.mx, c.Ms * c.my, c.Ms * c.mz);
+  if (MODE == XM_HEFF) {
+    float* o = lp.out + 3 * f.cell0;
+    o[i] = c.hx;
+    o[N + i] = c.hy;
+    o[2 * N + i] = c.hz;
+    return make_float3(c.Ms * c.mx, c.Ms * c.my, c.Ms * c.mz);
+  }
+  // Eq. 3: dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)], then renormalise
+  const float mx = c.mx, my = c.my, mz = c.mz;
+  const float3 p = cross3(mx, my, mz, c.hx, c.hy, c.hz);
+  const float3 q = cross3(mx, my, mz, p.x, p.y, p.z);
+  const float cdt = f.llg_c * lp.dt;
+  float ux = fmaf(cdt, fmaf(f.alpha, q.x, p.x), mx);
+  float uy = fmaf(cdt, fmaf(f.alpha, q.y, p.y), my);
+  float uz = fmaf(cdt, fmaf(f.alpha, q.z, p.z), mz);
+  const float inv = 1.0f / sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+  ux *= inv;
+  uy *= inv;
+  uz *= inv;
+  float* mo = lp.parity ? f.m0 : f.m1;
+  mo[i] = ux;
+  mo[N + i] = uy;
+  mo[2 * N + i] = uz;
+  return make_float3(c.Ms * ux, c.Ms * uy, c.Ms * uz);
+}
+
+// First pointwise half of the adjoint of one step m' = normalise(m + dt f(m, H(m))):
+// with lambda' = dL/dm', u = m + dt f, c = gamma0/(1+alpha^2),
+//   mu     = (lambda' - m'(m'.lambda'))/|u|
+//   nu     = dt c (m x mu - alpha m x (m x mu))                    (= dt (df/dH)^T mu)
+//   lambda_part = mu + dt c(-H x mu + alpha(-(m x H) x mu + H x (m x mu)))
+//                 + (2Ku/(mu0 Ms)) nu_x x                          (f and H_anis terms)
+// Accumulates dL/dH_ext += nu and the local part of dL/dMs, -nu.(H_exch + H_anis)/Ms;
+// stores lambda_part and nu and returns nu (unit weight), the next demag input.
+__device__ __forceinline__ float3 adj1_cell(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
+                                            int i, int x, int y, int z, float hdx, float hdy, float hdz) {
+  const int N = f.ncell;
+  const long long o = 3 * f.cell0;
+  const CellState loc = cell_field(f, 2u | 4u, m, i, x, y, z, 0.f, 0.f, 0.f);   // H_exch + H_anis
+  const CellState ext = cell_field(f, 8u, m, i, x, y, z, 0.f, 0.f, 0.f);        // H_ext
+  const float mx = loc.mx, my = loc.my, mz = loc.mz, Ms = loc.Ms;
+  const float Hx = hdx + loc.hx + ext.hx, Hy = hdy + loc.hy + ext.hy, Hz = hdz + loc.hz + ext.hz;
+  const float3 p = cross3(mx, my, mz, Hx, Hy, Hz);               // m x H
+  const float3 q = cross3(mx, my, mz, p.x, p.y, p.z);            // m x (m x H)
+  const float cdt = f.llg_c * lp.dt;                             // -dt c
+  const float ux = fmaf(cdt, fmaf(f.alpha, q.x, p.x), mx);
+  const float uy = fmaf(cdt, fmaf(f.alpha, q.y, p.y), my);
+  const float uz = fmaf(cdt, fmaf(f.alpha, q.z, p.z), mz);
+  const float inv = 1.0f / sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+  const float m1x = ux * inv, m1y = uy * inv, m1z = uz * inv;
+  const float* li = lp.adj_lam_in + o;
+  const float lx = li[i], ly = li[N + i], lz = li[2 * N + i];
+  const float d = m1x * lx + m1y * ly + m1z * lz;
+  const float mux = (lx - m1x * d) * inv, muy = (ly - m1y * d) * inv, muz = (lz - m1z * d) * inv;
+  const float3 a = cross3(mx, my, mz, mux, muy, muz);            // m x mu
+  const float3 b = cross3(mx, my, mz, a.x, a.y, a.z);            // m x (m x mu)
+  const float dtc = -cdt;
+  const float nx_ = dtc * (a.x - f.alpha * b.x), ny_ = dtc * (a.y - f.alpha * b.y),
+              nz_ = dtc * (a.z - f.alpha * b.z);
+  const float3 t1 = cross3(Hx, Hy, Hz, mux, muy, muz);           // H x mu
+  const float3 t2 = cross3(p.x, p.y, p.z, mux, muy, muz);        // (m x H) x mu
+  const float3 t3 = cross3(Hx, Hy, Hz, a.x, a.y, a.z);           // H x (m x mu)
+  float lpx = mux + dtc * (-t1.x + f.alpha * (t3.x - t2.x));
+  const float lpy = muy + dtc * (-t1.y + f.alpha * (t3.y - t2.y));
+  const float lpz = muz + dtc * (-t1.z + f.alpha * (t3.z - t2.z));
+  lpx = fmaf(f.can / Ms, nx_, lpx);
+  float* lp_ = lp.adj_lam_part + o;
+  lp_[i] = lpx;
+  lp_[N + i] = lpy;
+  lp_[2 * N + i] = lpz;
+  float* nu = lp.adj_nu + o;
+  nu[i] = nx_;
+  nu[N + i] = ny_;
+  nu[2 * N + i] = nz_;
+  if (lp.adj_g_hext) {
+    float* g = lp.adj_g_hext + o;
+    g[i] += nx_;
+    g[N + i] += ny_;
+    g[2 * N + i] += nz_;
+  }
+  if (lp.adj_g_ms) lp.adj_g_ms[f.cell0 + i] -= (nx_ * loc.hx + ny_ * loc.hy + nz_ * loc.hz) / Ms;
+  return make_float3(nx_, ny_, nz_);
+}
+
+// Second pointwise half: with D = -N * nu (the demag convolution of nu, unit weights),
+//   lambda = lambda_part + Ms D + L(C nu),  C = diag(2A/(mu0 Ms_i))   (D and exchange terms)
+//   dL/dMs += m . D
+__device__ __forceinline__ void adj2_cell(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
+                                          int i, int x, int y, int z, float dx, float dy, float dz) {
+  const int N = f.ncell;
+  const long long o = 3 * f.cell0;
+  const float Ms = cell_ms(f, i);
+  const float* nu = lp.adj_nu + o;
+  float3 l = make_float3(0.f, 0.f, 0.f);
+  if (f.cex != 0.f) {
+    if (f.ms_field) l = laplacian<true>(f, nu, i, x, y, z, f.cex / Ms, f.cex);
+    else {
+      l = laplacian<false>(f, nu, i, x, y, z, 1.f, 0.f);
+      const float c = f.cex / Ms;
+      l = make_float3(c * l.x, c * l.y, c * l.z);
+    }
+  }
+  const float* lpart = lp.adj_lam_part + o;
+  float* lo = lp.adj_lam_out + o;
+  lo[i] = lpart[i] + fmaf(Ms, dx, l.x);
+  lo[N + i] = lpart[N + i] + fmaf(Ms, dy, l.y);
+  lo[2 * N + i] = lpart[2 * N + i] + fmaf(Ms, dz, l.z);
+  if (lp.adj_g_ms) lp.adj_g_ms[f.cell0 + i] += m[i] * dx + m[N + i] * dy + m[2 * N + i] * dz;
+}
+
+}  // namespace grace

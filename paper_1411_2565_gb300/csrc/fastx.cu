@@ -10,96 +10,12 @@
 // stages the spectrum for the Hermitian merge/split and carries the FFT exchanges.
 #include <cuda_runtime.h>
 
+#include "cell.cuh"
 #include "fftreg.cuh"
 #include "internal.cuh"
 
 namespace grace {
 namespace {
-
-// Per-cell part of H_eff (exchange, anisotropy, Zeeman) added to the demag field in hd;
-// returns m and the total field.  All global loads of a cell happen here, so callers
-// batch several cells' calls before consuming the results.
-struct CellState {
-  float mx, my, mz, Ms, hx, hy, hz;
-};
-
-__device__ __forceinline__ CellState cell_field(const FilmDev& f, unsigned mask, const float* __restrict__ m,
-                                                int i, int x, int y, int z, float hdx, float hdy, float hdz) {
-  const int nx = f.nx, ny = f.ny, nz = f.nz, N = f.ncell;
-  CellState c;
-  c.mx = m[i];
-  c.my = m[N + i];
-  c.mz = m[2 * N + i];
-  c.Ms = f.ms_field ? f.ms_field[i] : f.Ms;
-  float hx = hdx, hy = hdy, hz = hdz;
-  if (mask & 2u) {
-    // six-neighbour Laplacian, sum of (m_j - m_i)/d^2, free boundaries
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    if (x > 0) { ax += m[i - 1] - c.mx; ay += m[N + i - 1] - c.my; az += m[2 * N + i - 1] - c.mz; }
-    if (x < nx - 1) { ax += m[i + 1] - c.mx; ay += m[N + i + 1] - c.my; az += m[2 * N + i + 1] - c.mz; }
-    float lx = ax * f.idx2, ly = ay * f.idx2, lz = az * f.idx2;
-    ax = ay = az = 0.f;
-    if (y > 0) { ax += m[i - nx] - c.mx; ay += m[N + i - nx] - c.my; az += m[2 * N + i - nx] - c.mz; }
-    if (y < ny - 1) { ax += m[i + nx] - c.mx; ay += m[N + i + nx] - c.my; az += m[2 * N + i + nx] - c.mz; }
-    lx = fmaf(ax, f.idy2, lx); ly = fmaf(ay, f.idy2, ly); lz = fmaf(az, f.idy2, lz);
-    const int pl = nx * ny;
-    ax = ay = az = 0.f;
-    if (z > 0) { ax += m[i - pl] - c.mx; ay += m[N + i - pl] - c.my; az += m[2 * N + i - pl] - c.mz; }
-    if (z < nz - 1) { ax += m[i + pl] - c.mx; ay += m[N + i + pl] - c.my; az += m[2 * N + i + pl] - c.mz; }
-    lx = fmaf(ax, f.idz2, lx); ly = fmaf(ay, f.idz2, ly); lz = fmaf(az, f.idz2, lz);
-    const float ce = f.cex / c.Ms;
-    hx = fmaf(ce, lx, hx);
-    hy = fmaf(ce, ly, hy);
-    hz = fmaf(ce, lz, hz);
-  }
-  if (mask & 4u) hx = fmaf(f.can / c.Ms, c.mx, hx);
-  if (mask & 8u) {
-    hx += f.hx;
-    hy += f.hy;
-    hz += f.hz;
-    if (f.h_field) {
-      hx += f.h_field[i];
-      hy += f.h_field[N + i];
-      hz += f.h_field[2 * N + i];
-    }
-  }
-  c.hx = hx;
-  c.hy = hy;
-  c.hz = hz;
-  return c;
-}
-
-// Writes the cell's result (H for XM_HEFF, m_{n+1} for XM_STEP) and returns Ms m of the
-// state the next spectrum is built from.
-template <int MODE>
-__device__ __forceinline__ float3 cell_apply(const FilmDev& f, const LaunchP& lp, int i, const CellState& c) {
-  const int N = f.ncell;
-  if (MODE == XM_R2C) return make_float3(c.Ms * c.mx, c.Ms * c.my, c.Ms * c.mz);
-  if (MODE == XM_HEFF) {
-    float* o = lp.out + 3 * f.cell0;
-    o[i] = c.hx;
-    o[N + i] = c.hy;
-    o[2 * N + i] = c.hz;
-    return make_float3(c.Ms * c.mx, c.Ms * c.my, c.Ms * c.mz);
-  }
-  // Eq. 3: dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)], then renormalise
-  const float mx = c.mx, my = c.my, mz = c.mz, hx = c.hx, hy = c.hy, hz = c.hz;
-  const float px = my * hz - mz * hy, py = mz * hx - mx * hz, pz = mx * hy - my * hx;
-  const float qx = my * pz - mz * py, qy = mz * px - mx * pz, qz = mx * py - my * px;
-  const float cdt = f.llg_c * lp.dt;
-  float ux = fmaf(cdt, fmaf(f.alpha, qx, px), mx);
-  float uy = fmaf(cdt, fmaf(f.alpha, qy, py), my);
-  float uz = fmaf(cdt, fmaf(f.alpha, qz, pz), mz);
-  const float inv = 1.0f / sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
-  ux *= inv;
-  uy *= inv;
-  uz *= inv;
-  float* mo = lp.parity ? f.m0 : f.m1;
-  mo[i] = ux;
-  mo[N + i] = uy;
-  mo[2 * N + i] = uz;
-  return make_float3(c.Ms * ux, c.Ms * uy, c.Ms * uz);
-}
 
 // Line-buffer stride for TY y lines of 3 components (line (t, c) at (3 t + c) * LS):
 // the staging and store loops run t fastest, so 3 LS must put the TY lines of one k on
@@ -136,11 +52,12 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
   float2* sm = reinterpret_cast<float2*>(smem4);
   float2* lines = sm + 3 * ty * LS;                              // this thread's 3 lines
   float* hs = reinterpret_cast<float*>(sm + 3 * TY * LS);        // [3][TY][Q]
-  const float* __restrict__ m = lp.parity ? f.m1 : f.m0;
+  const float* __restrict__ m = lp.mk ? lp.mk + 3 * f.cell0 : (lp.parity ? f.m1 : f.m0);
   const size_t srow = f.srow;
   const size_t sc = (size_t)nz * f.Kx * srow;                    // component stride of S
   float2* Sz = f.S + (size_t)z * f.Kx * srow;                    // S[c=0][z][.][.]
-  const bool demag = (MODE == XM_STEP) || (MODE == XM_HEFF && (lp.mask & 1u));
+  const bool demag = (MODE == XM_STEP) || (MODE == XM_ADJ1) || (MODE == XM_ADJ2) ||
+                     (MODE == XM_HEFF && (lp.mask & 1u));
   const int nst = 3 * (Q + 1) * TY;
 
   if (demag) {
@@ -190,9 +107,24 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
   }
   __syncthreads();
 
+  if constexpr (MODE == XM_ADJ1 || MODE == XM_ADJ2) {
+    // adjoint halves: H_demag(m_k) -> lambda_part, nu (R2C of nu follows), or D(nu) -> lambda_k
+    for (int idx = tid; idx < TY * Q; idx += NT) {
+      const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+      float* hp = hs + t * Q + x;
+      float3 r = make_float3(0.f, 0.f, 0.f);
+      if (x < nx && y < ny) {
+        const int i = (z * ny + y) * nx + x;
+        if (MODE == XM_ADJ1) r = adj1_cell(f, lp, m, i, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q]);
+        else adj2_cell(f, lp, m, i, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q]);
+      }
+      hp[0] = r.x;
+      hp[TY * Q] = r.y;
+      hp[2 * TY * Q] = r.z;
+    }
+  } else {
   // cell update, one thread per cell of the TY x Q tile (x >= nx, y >= ny give zeros);
   // each thread owns 8 cells and issues the loads of 4 of them before using any
-  {
     const unsigned mask = (MODE == XM_STEP) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
     constexpr int U = 4;
     for (int base = 0; base < TY * Q; base += U * NT) {
@@ -222,7 +154,7 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
       }
     }
   }
-  const bool r2c = (MODE != XM_HEFF) || demag;
+  const bool r2c = (MODE != XM_HEFF && MODE != XM_ADJ2) || (MODE == XM_HEFF && demag);
   if (!r2c) return;
   __syncthreads();
   {
@@ -270,6 +202,8 @@ cudaError_t launch_q(int mode, const FilmDev* films, const LaunchP& lp, int nuni
   switch (mode) {
     case XM_R2C: kx_fast<Q, XM_R2C><<<nunits, threads, smem, s>>>(films, lp); break;
     case XM_HEFF: kx_fast<Q, XM_HEFF><<<nunits, threads, smem, s>>>(films, lp); break;
+    case XM_ADJ1: kx_fast<Q, XM_ADJ1><<<nunits, threads, smem, s>>>(films, lp); break;
+    case XM_ADJ2: kx_fast<Q, XM_ADJ2><<<nunits, threads, smem, s>>>(films, lp); break;
     default: kx_fast<Q, XM_STEP><<<nunits, threads, smem, s>>>(films, lp); break;
   }
   return cudaGetLastError();
@@ -281,6 +215,8 @@ cudaError_t attr_q(size_t smem) {
   cudaError_t e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_R2C>, a, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_HEFF>, a, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_STEP>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_ADJ1>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_ADJ2>, a, (int)smem);
   return e;
 }
 

@@ -15,6 +15,7 @@
 // with the usual split / merge twiddles W^k = exp(-2 pi i k / P).
 #include <cuda_runtime.h>
 
+#include "cell.cuh"
 #include "fft.cuh"
 #include "internal.cuh"
 
@@ -45,10 +46,11 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
   float* rb = reinterpret_cast<float*>(cb + TY * lsx);     // [3][TY][nx]
   const int tid = threadIdx.x, NT = blockDim.x;
   const int N = f.ncell;
-  const float* __restrict__ m = lp.parity ? f.m1 : f.m0;
+  const float* __restrict__ m = lp.mk ? lp.mk + 3 * f.cell0 : (lp.parity ? f.m1 : f.m0);
   const int twq = Q > 0 ? GRACE_LMAX / (2 * Q) : 0;      // table step for W^k, P = 2Q
 
-  const bool demag = (MODE == XM_STEP) || (MODE == XM_HEFF && (lp.mask & 1u));
+  const bool demag = (MODE == XM_STEP) || (MODE == XM_ADJ1) || (MODE == XM_ADJ2) ||
+                     (MODE == XM_HEFF && (lp.mask & 1u));
   if (demag) {
     for (int c = 0; c < 3; ++c) {
       if (Q == 0) {
@@ -99,92 +101,27 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
     float* r0 = rb + (0 * TY + ty) * nx + x;
     float* r1 = rb + (1 * TY + ty) * nx + x;
     float* r2 = rb + (2 * TY + ty) * nx + x;
-    if (y >= ny) {
-      *r0 = 0.f;
-      *r1 = 0.f;
-      *r2 = 0.f;
-      continue;
-    }
-    const int i = (z * ny + y) * nx + x;
-    const float mx = m[i], my = m[N + i], mz = m[2 * N + i];
-    const float Ms = f.ms_field ? f.ms_field[i] : f.Ms;
-    if (MODE == XM_R2C) {
-      *r0 = Ms * mx;
-      *r1 = Ms * my;
-      *r2 = Ms * mz;
-      continue;
-    }
-    const unsigned mask = (MODE == XM_STEP) ? 15u : lp.mask;
-    float hx = 0.f, hy = 0.f, hz = 0.f;
-    if (mask & 1u) {
-      hx = *r0;
-      hy = *r1;
-      hz = *r2;
-    }
-    if (mask & 2u) {
-      // six-neighbour Laplacian, sum of (m_j - m_i)/d^2, free boundaries
-      float lx = 0.f, ly = 0.f, lz = 0.f;
-      float ax = 0.f, ay = 0.f, az = 0.f;
-      if (x > 0) { ax += m[i - 1] - mx; ay += m[N + i - 1] - my; az += m[2 * N + i - 1] - mz; }
-      if (x < nx - 1) { ax += m[i + 1] - mx; ay += m[N + i + 1] - my; az += m[2 * N + i + 1] - mz; }
-      lx = ax * f.idx2; ly = ay * f.idx2; lz = az * f.idx2;
-      ax = ay = az = 0.f;
-      if (y > 0) { ax += m[i - nx] - mx; ay += m[N + i - nx] - my; az += m[2 * N + i - nx] - mz; }
-      if (y < ny - 1) { ax += m[i + nx] - mx; ay += m[N + i + nx] - my; az += m[2 * N + i + nx] - mz; }
-      lx = fmaf(ax, f.idy2, lx); ly = fmaf(ay, f.idy2, ly); lz = fmaf(az, f.idy2, lz);
-      const int pl = nx * ny;
-      ax = ay = az = 0.f;
-      if (z > 0) { ax += m[i - pl] - mx; ay += m[N + i - pl] - my; az += m[2 * N + i - pl] - mz; }
-      if (z < nz - 1) { ax += m[i + pl] - mx; ay += m[N + i + pl] - my; az += m[2 * N + i + pl] - mz; }
-      lx = fmaf(ax, f.idz2, lx); ly = fmaf(ay, f.idz2, ly); lz = fmaf(az, f.idz2, lz);
-      const float ce = f.cex / Ms;
-      hx = fmaf(ce, lx, hx);
-      hy = fmaf(ce, ly, hy);
-      hz = fmaf(ce, lz, hz);
-    }
-    if (mask & 4u) hx = fmaf(f.can / Ms, mx, hx);
-    if (mask & 8u) {
-      hx += f.hx;
-      hy += f.hy;
-      hz += f.hz;
-      if (f.h_field) {
-        hx += f.h_field[i];
-        hy += f.h_field[N + i];
-        hz += f.h_field[2 * N + i];
+    float3 r = make_float3(0.f, 0.f, 0.f);
+    if (y < ny) {
+      const int i = (z * ny + y) * nx + x;
+      const float hdx = demag ? *r0 : 0.f, hdy = demag ? *r1 : 0.f, hdz = demag ? *r2 : 0.f;
+      if constexpr (MODE == XM_ADJ1) {
+        r = adj1_cell(f, lp, m, i, x, y, z, hdx, hdy, hdz);
+      } else if constexpr (MODE == XM_ADJ2) {
+        adj2_cell(f, lp, m, i, x, y, z, hdx, hdy, hdz);
+      } else {
+        const unsigned mask = (MODE == XM_STEP) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
+        const CellState cs = cell_field(f, mask, m, i, x, y, z, hdx, hdy, hdz);
+        r = cell_apply<MODE>(f, lp, i, cs);
       }
     }
-    if (MODE == XM_HEFF) {
-      float* o = lp.out + 3 * f.cell0;
-      o[i] = hx;
-      o[N + i] = hy;
-      o[2 * N + i] = hz;
-      *r0 = Ms * mx;
-      *r1 = Ms * my;
-      *r2 = Ms * mz;
-    } else {
-      // Eq. 3: dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)]
-      const float px = my * hz - mz * hy, py = mz * hx - mx * hz, pz = mx * hy - my * hx;
-      const float qx = my * pz - mz * py, qy = mz * px - mx * pz, qz = mx * py - my * px;
-      const float cdt = f.llg_c * lp.dt;
-      float ux = fmaf(cdt, fmaf(f.alpha, qx, px), mx);
-      float uy = fmaf(cdt, fmaf(f.alpha, qy, py), my);
-      float uz = fmaf(cdt, fmaf(f.alpha, qz, pz), mz);
-      const float inv = 1.0f / sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
-      ux *= inv;
-      uy *= inv;
-      uz *= inv;
-      float* mo = lp.parity ? f.m0 : f.m1;
-      mo[i] = ux;
-      mo[N + i] = uy;
-      mo[2 * N + i] = uz;
-      *r0 = Ms * ux;
-      *r1 = Ms * uy;
-      *r2 = Ms * uz;
-    }
+    *r0 = r.x;
+    *r1 = r.y;
+    *r2 = r.z;
   }
   __syncthreads();
 
-  const bool r2c = (MODE != XM_HEFF) || demag;
+  const bool r2c = (MODE != XM_HEFF && MODE != XM_ADJ2) || (MODE == XM_HEFF && demag);
   if (!r2c) return;
   for (int c = 0; c < 3; ++c) {
     if (Q == 0) {
@@ -515,6 +452,8 @@ cudaError_t configure_kernels(size_t smem_x, size_t smem_yz, size_t smem_y, size
   set((const void*)k_xpass<XM_R2C>, smem_x);
   set((const void*)k_xpass<XM_HEFF>, smem_x);
   set((const void*)k_xpass<XM_STEP>, smem_x);
+  set((const void*)k_xpass<XM_ADJ1>, smem_x);
+  set((const void*)k_xpass<XM_ADJ2>, smem_x);
   set((const void*)k_yz, smem_yz);
   set((const void*)k_y<-1>, smem_y);
   set((const void*)k_y<+1>, smem_y);
@@ -528,6 +467,8 @@ cudaError_t launch_xpass(int mode, const FilmDev* films, const LaunchP& lp, int 
   switch (mode) {
     case XM_R2C: k_xpass<XM_R2C><<<nunits, kThreads, smem, s>>>(films, lp); break;
     case XM_HEFF: k_xpass<XM_HEFF><<<nunits, kThreads, smem, s>>>(films, lp); break;
+    case XM_ADJ1: k_xpass<XM_ADJ1><<<nunits, kThreads, smem, s>>>(films, lp); break;
+    case XM_ADJ2: k_xpass<XM_ADJ2><<<nunits, kThreads, smem, s>>>(films, lp); break;
     default: k_xpass<XM_STEP><<<nunits, kThreads, smem, s>>>(films, lp); break;
   }
   return cudaGetLastError();

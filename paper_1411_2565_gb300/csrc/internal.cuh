@@ -53,7 +53,8 @@ struct FilmDev {
   const float* h_field;    // per-cell H_ext of this film or nullptr
 };
 
-enum XMode { XM_R2C = 0, XM_HEFF = 1, XM_STEP = 2 };
+// x-pass modes: R2C of Ms m; H_eff output; Euler step; the two halves of the adjoint.
+enum XMode { XM_R2C = 0, XM_HEFF = 1, XM_STEP = 2, XM_ADJ1 = 3, XM_ADJ2 = 4 };
 
 struct LaunchP {
   int nfilms;
@@ -65,6 +66,14 @@ struct LaunchP {
   int RPB;          // rows per block in the split y pass
   int TQ;           // columns per block in the split z pass
   const float2* tw; // twiddle table, GRACE_LMAX entries
+  // adjoint (concatenated films; nullptr when unused)
+  const float* mk;          // state to read instead of m[parity] (R2C, ADJ1, ADJ2)
+  const float* adj_lam_in;  // lambda_{k+1}
+  float* adj_lam_part;      // ADJ1 -> ADJ2
+  float* adj_nu;            // ADJ1 -> ADJ2
+  float* adj_lam_out;       // lambda_k
+  float* adj_g_hext;        // += dL/dH_ext (3 N) or nullptr
+  float* adj_g_ms;          // += dL/dMs (N) or nullptr
 };
 
 // Film owning work unit `unit` of kind `kind` (films sorted by u0[kind]).

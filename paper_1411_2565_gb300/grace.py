@@ -114,6 +114,26 @@ class _Base:
     def step(self, n: int, dt: float):
         check(self._L.grace_step(self.ctx, int(n), float(dt)), "grace_step", self.ctx)
 
+    def backward(self, dL_dmT: torch.Tensor, n: int, dt: float, ckpt_every: int = 64,
+                 g_hext: Optional[torch.Tensor] = None, g_ms: Optional[torch.Tensor] = None,
+                 want_m0: bool = True) -> Optional[torch.Tensor]:
+        """Discrete adjoint of ``n`` Euler steps from the current state (grace_backward).
+
+        Adds dL/dH_ext into ``g_hext`` (3N) and dL/dMs into ``g_ms`` (N) when given and
+        returns dL/dm_0; the state is left at m_0."""
+        sz = C.c_size_t()
+        check(self._L.grace_backward_workspace_size(self.ctx, int(n), int(ckpt_every), C.byref(sz)),
+              "grace_backward_workspace_size", self.ctx)
+        scratch = torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=self.device)
+        gm0 = torch.empty(3 * self.ncell, dtype=torch.float32, device=self.device) if want_m0 else None
+        check(self._L.grace_backward(
+            self.ctx, _dev_ptr(dL_dmT, 3 * self.ncell, "dL/dm_T"), int(n), float(dt), int(ckpt_every),
+            scratch.data_ptr(), int(sz.value),
+            None if g_hext is None else _dev_ptr(g_hext, 3 * self.ncell, "g_hext"),
+            None if g_ms is None else _dev_ptr(g_ms, self.ncell, "g_ms"),
+            None if gm0 is None else gm0.data_ptr()), "grace_backward", self.ctx)
+        return gm0
+
     def energy(self):
         e = (C.c_double * 5)()
         mv = (C.c_double * 3)()

@@ -1,0 +1,115 @@
+"""Adjoint LLG on the GPU (grace_backward) against the FP64 oracle's exact discrete adjoint.
+
+The oracle adjoint is itself pinned by central finite differences of the FP64 forward map
+(tests/test_oracle_pins.py).  The GPU runs FP32, so forward states differ from the
+oracle's by rounding; gradients are compared in relative L2 norm (bar 1e-3)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import adjoint as oadj
+from oracle import llg
+from paper_1411_2565_gb300 import build as libbuild
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    libbuild.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def setup(grid, cell, steps, seed=5, Ku=0.0):
+    from paper_1411_2565_gb300.grace import Grace
+    f, m0 = workloads.small_film(grid, cell=cell, seed=seed, Ms=8e5, A=1.3e-11, Ku=Ku, alpha=0.1)
+    shape = f.shape_zyx
+    n = int(np.prod(shape))
+    ms = (8e5 * (1 + 0.1 * (2 * workloads.uniform(seed + 1, n) - 1))).astype(np.float32).reshape(shape)
+    h = (2e4 * (2 * workloads.uniform(seed + 2, 3 * n) - 1)).astype(np.float32).reshape((3,) + shape)
+    target = workloads.smooth_target(shape, seed + 3)
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=DEV)
+    return f, m0, ms, h, target, g
+
+
+def oracle_grads(f, m0, ms, h, target, dt, steps):
+    p = llg.Params(f.cell, ms.astype(np.float64), f.A, f.Ku, f.alpha, f.gamma0, h.astype(np.float64))
+    return oadj.gradients(m0, p, dt, steps, target)
+
+
+@pytest.mark.parametrize("grid,steps,ckpt", [((24, 16, 2), 37, 8), ((20, 12, 1), 30, 30),
+                                             ((12, 10, 6), 20, 7)])
+def test_backward_matches_fp64_adjoint(grid, steps, ckpt):
+    dt = 1e-14
+    f, m0, ms, h, target, g = setup(grid, (4e-9, 4e-9, 3e-9), steps, Ku=2e3)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(DEV)
+    g.set_ms_field(dev(ms))
+    g.set_hext_field(dev(h))
+    g.set_m(dev(m0))
+    g.step(steps, dt)
+    mT = g.get_m()
+    n = mT.numel() // 3
+    lamT = 2.0 * (mT - dev(target)) / n
+    g.set_m(dev(m0))
+    gh = torch.zeros(3 * n, device=DEV)
+    gms = torch.zeros(n, device=DEV)
+    gm0 = g.backward(lamT, steps, dt, ckpt, gh, gms)
+    loss, o_m0, o_h, o_ms = oracle_grads(f, m0, ms, h, target, dt, steps)
+    assert rel(gh.cpu().numpy(), o_h) <= 1e-3
+    assert rel(gms.cpu().numpy(), o_ms) <= 1e-3
+    assert rel(gm0.cpu().numpy(), o_m0) <= 1e-3
+    # the state is left at m_0
+    assert torch.equal(g.get_m(), dev(m0))
+
+
+def test_autograd_function_matches_direct_backward():
+    from paper_1411_2565_gb300.autograd import llg as llg_fn
+    dt, steps = 1e-14, 24
+    f, m0, ms, h, target, g = setup((16, 12, 2), (4e-9, 4e-9, 3e-9), steps)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(DEV)
+    m0t = dev(m0).requires_grad_(True)
+    ht = dev(h).requires_grad_(True)
+    mst = dev(ms).requires_grad_(True)
+    mT = llg_fn(m0t, ht, mst, g, steps, dt, 10)
+    loss = ((mT - dev(target)) ** 2).sum() / (mT.numel() // 3)
+    loss.backward()
+    _, o_m0, o_h, o_ms = oracle_grads(f, m0, ms, h, target, dt, steps)
+    assert rel(ht.grad.cpu().numpy(), o_h) <= 1e-3
+    assert rel(mst.grad.cpu().numpy(), o_ms) <= 1e-3
+    assert rel(m0t.grad.cpu().numpy(), o_m0) <= 1e-3
+
+
+def test_adjoint_workload_full_grid():
+    """The 256x64x2 adjoint film (4x4x3 nm cells, per-cell Ms and field) for 128 steps with
+    checkpoints every 64, against the FP64 adjoint."""
+    w = workloads.adjoint_film()
+    f, m0 = w.films[0], w.m0[0]
+    from paper_1411_2565_gb300.grace import Grace
+    steps, dt = 128, w.dt
+    shape = f.shape_zyx
+    ms = w.ms_field
+    h = np.zeros((3,) + shape, dtype=np.float32)
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=DEV)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(DEV)
+    g.set_ms_field(dev(ms))
+    g.set_hext_field(dev(h))
+    g.set_m(dev(m0))
+    g.step(steps, dt)
+    mT = g.get_m()
+    n = mT.numel() // 3
+    lamT = 2.0 * (mT - dev(w.target)) / n
+    g.set_m(dev(m0))
+    gh = torch.zeros(3 * n, device=DEV)
+    gms = torch.zeros(n, device=DEV)
+    gm0 = g.backward(lamT, steps, dt, 64, gh, gms)
+    _, o_m0, o_h, o_ms = oracle_grads(f, m0, ms, h, w.target, dt, steps)
+    assert rel(gh.cpu().numpy(), o_h) <= 1e-3
+    assert rel(gms.cpu().numpy(), o_ms) <= 1e-3
+    assert rel(gm0.cpu().numpy(), o_m0) <= 1e-3
