@@ -74,7 +74,9 @@ enum {
   GRACE_KERNEL_YZ = 2,        /* the same two passes with runtime lengths (small or mixed films) */
   GRACE_KERNEL_Y = 3,         /* split path for thick films: y FFT (both directions) */
   GRACE_KERNEL_Z = 4,         /* split path: z FFT + tensor product + inverse z */
-  GRACE_KERNEL_X = 5          /* runtime-length x pass */
+  GRACE_KERNEL_X = 5,         /* runtime-length x pass */
+  GRACE_KERNEL_Y_FAST = 6,    /* split path, compile-time length: y FFT (both directions) */
+  GRACE_KERNEL_Z_FAST = 7     /* split path, compile-time length: z FFT + tensor product + inverse */
 };
 
 /*

@@ -55,9 +55,10 @@ constexpr int kEnergyBlocks = 304;
 // lengths, or one generic group (runtime lengths) for everything else.
 struct Group {
   std::vector<int> idx;
-  bool fast = false;
+  bool fast = false;        // compile-time FFT lengths (fused y-z, or split when split_fast)
+  bool split_fast = false;  // fast x pass + fast y rows + fast z columns (films with nz > 4)
   bool fused = true;
-  int Q = 0, Py = 0, nz = 0;
+  int Q = 0, Py = 0, nz = 0, Pz = 0;
   int TY = 1, KPB = 1, RPB = 1, TQ = 1;
   int units[UK_COUNT] = {0, 0, 0, 0, 0};
   size_t smem_x = 0, smem_yz = 0, smem_y = 0, smem_z = 0;
@@ -65,7 +66,7 @@ struct Group {
   std::vector<FilmDev> fd;
 };
 
-enum TraceKind { TK_YZ_FAST = 0, TK_X_FAST, TK_YZ, TK_Y, TK_Z, TK_X, TK_COUNT };
+enum TraceKind { TK_YZ_FAST = 0, TK_X_FAST, TK_YZ, TK_Y, TK_Z, TK_X, TK_Y_FAST, TK_Z_FAST, TK_COUNT };
 
 struct grace_ctx {
   std::vector<FilmHost> films;
@@ -150,7 +151,14 @@ int plan_group(grace_ctx* c, Group& g) {
     maxPy = std::max(maxPy, s.P[1]);
     if (s.zfft) maxPz = std::max(maxPz, s.P[2]);
   }
-  if (g.fast) {
+  if (g.split_fast) {
+    g.fused = false;
+    g.TY = fast_x_tile(g.Q);
+    g.smem_x = fast_x_smem(g.Q, g.TY);
+    g.RPB = fast_y_rows(g.Py);
+    g.TQ = fast_z_cols(g.Pz);
+    if (g.smem_x > kSmemMax) return GRACE_EUNSUPPORTED;
+  } else if (g.fast) {
     g.fused = true;
     g.TY = fast_x_tile(g.Q);   // compile-time tile of the fast x pass
     g.smem_x = fast_x_smem(g.Q, g.TY);
@@ -227,13 +235,17 @@ int plan(grace_ctx* c) {
   for (size_t i = 0; i < c->films.size(); ++i) {
     const FilmHost& f = c->films[i];
     const ShapeClass& s = c->classes[f.cls];
-    const int Q = s.P[0] / 2, Py = s.P[1], nz = f.n[2];
-    const bool fast = fast_x_supported(Q) && fast_yz_supported(Py, nz);
+    const int Q = s.P[0] / 2, Py = s.P[1], nz = f.n[2], Pz = s.P[2];
+    const bool fused_fast = fast_x_supported(Q) && fast_yz_supported(Py, nz);
+    const bool split_fast = !fused_fast && s.zfft && fast_x_supported(Q) && fast_split_supported(Py, Pz);
+    const bool fast = fused_fast || split_fast;
     int gi = -1;
     if (fast) {
       for (size_t k = 0; k < c->groups.size(); ++k) {
         const Group& g = c->groups[k];
-        if (g.fast && g.Q == Q && g.Py == Py && g.nz == nz) gi = (int)k;
+        if (g.fast && g.split_fast == split_fast && g.Q == Q && g.Py == Py &&
+            (split_fast ? g.Pz == Pz : g.nz == nz))
+          gi = (int)k;
       }
     } else {
       gi = generic;
@@ -241,9 +253,11 @@ int plan(grace_ctx* c) {
     if (gi < 0) {
       Group g;
       g.fast = fast;
+      g.split_fast = split_fast;
       g.Q = Q;
       g.Py = Py;
       g.nz = nz;
+      g.Pz = Pz;
       c->groups.push_back(g);
       gi = (int)c->groups.size() - 1;
       if (!fast) generic = gi;
@@ -303,7 +317,7 @@ int plan(grace_ctx* c) {
       d.u0[UK_X] = u[UK_X];
       u[UK_X] += d.nz * ((d.ny + g.TY - 1) / g.TY);
       d.u0[UK_YZ] = u[UK_YZ];
-      u[UK_YZ] += g.fast ? (d.Kx + g.KPB - 1) / g.KPB : d.Kx;
+      u[UK_YZ] += (g.fast && !g.split_fast) ? (d.Kx + g.KPB - 1) / g.KPB : d.Kx;
       d.u0[UK_Y] = u[UK_Y];
       u[UK_Y] += (3 * d.nz * d.Kx + g.RPB - 1) / g.RPB;
       d.u0[UK_Z] = u[UK_Z];
@@ -430,6 +444,12 @@ cudaError_t mark(grace_ctx* c, int kind, cudaStream_t s) {
 
 cudaError_t enqueue_conv(grace_ctx* c, const Group& g, const LaunchP& lp, cudaStream_t s) {
   const FilmDev* f = gfilms(c, g);
+  if (g.split_fast) {
+    GRACE_LAUNCH(c, TK_Y_FAST, s, launch_fast_y(g.Py, -1, f, lp, g.units[UK_Y], s));
+    GRACE_LAUNCH(c, TK_Z_FAST, s, launch_fast_z(g.Pz, f, lp, g.units[UK_Z], s));
+    GRACE_LAUNCH(c, TK_Y_FAST, s, launch_fast_y(g.Py, +1, f, lp, g.units[UK_Y], s));
+    return cudaSuccess;
+  }
   if (g.fast) {
     GRACE_LAUNCH(c, TK_YZ_FAST, s, launch_fast_yz(g.Py, g.nz, f, lp, g.units[UK_YZ], g.KPB, g.smem_yz, s));
     return cudaSuccess;
@@ -497,7 +517,9 @@ cudaError_t configure_all(grace_ctx* c) {
     cudaError_t e = cudaSuccess;
     if (g.fast) {
       e = configure_fast_x(g.Q, std::max<size_t>(g.smem_x, 1));
-      if (e == cudaSuccess) e = configure_fast_yz(g.Py, g.nz, std::max<size_t>(g.smem_yz, 1));
+      if (e == cudaSuccess)
+        e = g.split_fast ? configure_fast_split(g.Py, g.Pz)
+                         : configure_fast_yz(g.Py, g.nz, std::max<size_t>(g.smem_yz, 1));
       if (e != cudaSuccess) return e;
     } else {
       sx = std::max(sx, g.smem_x);

@@ -111,6 +111,12 @@ cudaError_t configure_fast_yz(int Py, int nz, size_t smem);
 cudaError_t launch_fast_yz(int Py, int nz, const FilmDev* films, const LaunchP& lp, int nunits, int kpb,
                            size_t smem, cudaStream_t s);
 cudaError_t configure_kernels(size_t smem_x, size_t smem_yz, size_t smem_y, size_t smem_z);
+bool fast_split_supported(int Py, int Pz);
+int fast_y_rows(int Py);
+int fast_z_cols(int Pz);
+cudaError_t configure_fast_split(int Py, int Pz);
+cudaError_t launch_fast_y(int Py, int dir, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s);
+cudaError_t launch_fast_z(int Pz, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s);
 
 struct TensorJob {
   int nx, ny, nz, Px, Py, Pz, Kx, Ky, Kz, zfft, nslot;

@@ -55,7 +55,7 @@ def make(f, m0, ms=None, hfield=None):
     return g
 
 
-GRIDS = [(24, 12, 2), (17, 5, 3), (1, 1, 1), (3, 1, 1), (1, 7, 1), (2, 2, 2), (8, 8, 1),
+GRIDS = [(24, 12, 2), (17, 5, 3), (1, 1, 1), (3, 1, 1), (1, 7, 1), (2, 2, 2), (8, 8, 1), (9, 3, 6), (5, 2, 7),
          (40, 20, 4), (16, 8, 6), (33, 9, 5), (5, 40, 1), (64, 3, 2), (130, 6, 1)]
 
 
