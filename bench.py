@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the block / ensemble / adjoint measurements")
     return ap.parse_args()
 
 
@@ -266,6 +268,9 @@ def run_grace(args, rank, world, local):
            "h2d_bytes_per_step": 12 * ncell, "d2h_bytes_per_step": 12 * ncell,
            "steps": args.e2e_steps, "path": "grace_set_m_host + grace_step(1) + grace_get_m_host"}
 
+    extras = None
+    if rank == 0 and not args.no_extras:
+        extras = extra_workloads(dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds)
@@ -279,13 +284,93 @@ def run_grace(args, rank, world, local):
                    "initial_state": w.note, "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}", "wall_s_timed_loop": round(wall, 3)},
         "roofline": roof, "kernels": kernels, "gpu_launches": launches, "e2e": e2e,
-        "cpu_baseline": cpu, "clocks": clk,
+        "cpu_baseline": cpu, "clocks": clk, "workloads": extras,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def time_events(fn, reps):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) * 1e-3
+
+
+def extra_workloads(dev):
+    """Throughput of the other forms of the hot path (thick block, film ensemble, adjoint)."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_1411_2565_gb300.grace import Grace, GraceBatch
+    out = {}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    # 256x256x64 block, FFT along z: 20 single steps, L2 flushed before each
+    w = workloads.block()
+    f, m0 = w.films[0], w.m0[0]
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=dev)
+    g.set_m(torch.from_numpy(m0.reshape(-1)).to(dev))
+    g.step(3, w.dt)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    g.trace(200)
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        g.step(1, w.dt)
+        b.record()
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    tr = g.trace_read()
+    g.trace(0)
+    out["block"] = {"workload": w.name, "value": f.ncells * 20 / t, "unit": UNIT, "ms_per_step": t / 20 * 1e3,
+                    "kernels_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in tr.items()},
+                    "method": "20 single steps, L2 flushed before each"}
+    del g
+    # 256-film ensemble, 2000 steps in replayed CUDA graphs (one grouped launch per kernel
+    # and size class per step)
+    w = workloads.ensemble()
+    gb = GraceBatch(w.films, device=dev)
+    gb.set_m(torch.from_numpy(np.concatenate([m.reshape(-1) for m in w.m0])).to(dev))
+    gb.step(32, w.dt)
+    t = time_events(lambda: gb.step(2000, w.dt), 1)
+    ncell = sum(f.ncells for f in w.films)
+    out["ensemble"] = {"workload": w.name, "films": len(w.films), "cells": ncell,
+                       "value": ncell * 2000 / t, "unit": UNIT, "ms_per_step": t / 2000 * 1e3,
+                       "method": "2000 steps back to back (graphs of 16 steps); ~300 MB working set"}
+    del gb
+    # adjoint film: 256 forward steps, then the backward pass (checkpoints every 64)
+    w = workloads.adjoint_film()
+    f, m0 = w.films[0], w.m0[0]
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=dev)
+    ms = torch.from_numpy(w.ms_field.reshape(-1)).to(dev)
+    h = torch.zeros(3 * f.ncells, device=dev)
+    g.set_ms_field(ms)
+    g.set_hext_field(h)
+    md = torch.from_numpy(m0.reshape(-1)).to(dev)
+    n = 256
+    g.set_m(md)
+    t_f = time_events(lambda: g.step(n, w.dt), 1)
+    lam = torch.full((3 * f.ncells,), 1e-6, device=dev)
+    gh = torch.zeros_like(h)
+    gm = torch.zeros_like(ms)
+    g.set_m(md)
+    g.backward(lam, n, w.dt, 64, gh, gm)        # warm-up (scratch allocation by torch)
+    t_b = time_events(lambda: g.backward(lam, n, w.dt, 64, gh, gm), 1)
+    out["adjoint"] = {"workload": w.name, "steps": n, "unit": UNIT,
+                      "forward_value": f.ncells * n / t_f, "backward_value": f.ncells * n / t_b,
+                      "fwd_plus_bwd_ms_per_step": (t_f + t_b) / n * 1e3,
+                      "method": "forward steps, then grace_backward with checkpoints every 64 "
+                                "(re-computes the forward inside)"}
+    return out
 
 
 def cpu_baseline(w, seconds):
