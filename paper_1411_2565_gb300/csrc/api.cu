@@ -87,6 +87,7 @@ struct grace_ctx {
   const float* ms_field = nullptr;
   const float* h_field = nullptr;
   bool use_graph = true;
+  bool pdl = true;
   int graph_steps = 16;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -300,6 +301,8 @@ int plan(grace_ctx* c) {
     d.Ms = (float)h.Ms;
     d.cex = (float)(2.0 * h.A / kMu0);
     d.can = (float)(2.0 * h.Ku / kMu0);
+    d.cex_ms = (float)(2.0 * h.A / (kMu0 * (double)d.Ms));
+    d.can_ms = (float)(2.0 * h.Ku / (kMu0 * (double)d.Ms));
     d.alpha = (float)h.alpha;
     d.llg_c = (float)(-h.gamma0 / (1.0 + h.alpha * h.alpha));
     d.hx = (float)h.h[0];
@@ -413,6 +416,7 @@ LaunchP group_lp(const grace_ctx* c, const Group& g) {
   lp.RPB = g.RPB;
   lp.TQ = g.TQ;
   lp.tw = reinterpret_cast<const float2*>(c->ws + c->o_tw);
+  lp.pdl = c->pdl ? 1 : 0;
   return lp;
 }
 
@@ -797,7 +801,11 @@ int grace_step(grace_ctx* c, int n, double dt) {
       cudaGraph_t g = nullptr;
       GRACE_CUDA(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
       cudaError_t e = cudaSuccess;
+      // inside a graph plain serialisation measured faster than programmatic edges
+      const bool pdl = c->pdl;
+      c->pdl = false;
       for (int s = 0; s < G && e == cudaSuccess; ++s) e = enqueue_step(c, (p + s) & 1, fdt, c->cap);
+      c->pdl = pdl;
       cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
       if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -964,6 +972,11 @@ int grace_set_option(grace_ctx* c, int option, long long value) {
       drop_graphs(c);
       if (c->use_graph && c->bound && !c->cap)
         GRACE_CUDA(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+      return GRACE_OK;
+    case GRACE_OPT_PDL:
+      if (value != 0 && value != 1) return fail(c, GRACE_EINVAL, "GRACE_OPT_PDL takes 0 or 1");
+      c->pdl = value != 0;
+      drop_graphs(c);
       return GRACE_OK;
     case GRACE_OPT_TILE_X:
     case GRACE_OPT_TILE_YZ: {

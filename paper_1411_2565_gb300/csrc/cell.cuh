@@ -12,6 +12,13 @@ struct CellState {
 
 __device__ __forceinline__ float cell_ms(const FilmDev& f, int i) { return f.ms_field ? f.ms_field[i] : f.Ms; }
 
+// 1/sqrt(s) for s near 1: hardware estimate refined by one Newton-Raphson step
+// r <- r (3 - s r^2)/2, which brings it to within about an ulp.
+__device__ __forceinline__ float rnorm(float s) {
+  const float r = rsqrtf(s);
+  return r * fmaf(-0.5f * s, r * r, 1.5f);
+}
+
 // Six-neighbour Laplacian of the vector field a (component stride N) at cell i, with
 // per-cell weights w (w == nullptr: weight 1): sum_d sum_j (w_j a_j - w_i a_i)/d^2,
 // free boundaries.  Differences are formed before the 1/d^2 scaling.
@@ -49,14 +56,15 @@ __device__ __forceinline__ CellState cell_field(const FilmDev& f, unsigned mask,
   c.mz = m[2 * N + i];
   c.Ms = cell_ms(f, i);
   float hx = hdx, hy = hdy, hz = hdz;
+  const float rms = f.ms_field ? __frcp_rn(c.Ms) : 0.f;
   if (mask & 2u) {
     const float3 l = laplacian<false>(f, m, i, x, y, z, 1.f, 0.f);
-    const float ce = f.cex / c.Ms;          // 2A/(mu0 Ms), observer cell
+    const float ce = f.ms_field ? f.cex * rms : f.cex_ms;    // 2A/(mu0 Ms), observer cell
     hx = fmaf(ce, l.x, hx);
     hy = fmaf(ce, l.y, hy);
     hz = fmaf(ce, l.z, hz);
   }
-  if (mask & 4u) hx = fmaf(f.can / c.Ms, c.mx, hx);
+  if (mask & 4u) hx = fmaf(f.ms_field ? f.can * rms : f.can_ms, c.mx, hx);
   if (mask & 8u) {
     hx += f.hx;
     hy += f.hy;
@@ -98,7 +106,7 @@ __device__ __forceinline__ float3 cell_apply(const FilmDev& f, const LaunchP& lp
   float ux = fmaf(cdt, fmaf(f.alpha, q.x, p.x), mx);
   float uy = fmaf(cdt, fmaf(f.alpha, q.y, p.y), my);
   float uz = fmaf(cdt, fmaf(f.alpha, q.z, p.z), mz);
-  const float inv = 1.0f / sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+  const float inv = rnorm(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
   ux *= inv;
   uy *= inv;
   uz *= inv;
@@ -131,7 +139,7 @@ __device__ __forceinline__ float3 adj1_cell(const FilmDev& f, const LaunchP& lp,
   const float ux = fmaf(cdt, fmaf(f.alpha, q.x, p.x), mx);
   const float uy = fmaf(cdt, fmaf(f.alpha, q.y, p.y), my);
   const float uz = fmaf(cdt, fmaf(f.alpha, q.z, p.z), mz);
-  const float inv = 1.0f / sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+  const float inv = rnorm(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));   // as in the forward step
   const float m1x = ux * inv, m1y = uy * inv, m1z = uz * inv;
   const float* li = lp.adj_lam_in + o;
   const float lx = li[i], ly = li[N + i], lz = li[2 * N + i];

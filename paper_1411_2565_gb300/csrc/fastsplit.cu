@@ -33,6 +33,8 @@ __global__ void __launch_bounds__(256) ky_fast(const FilmDev* __restrict__ films
   extern __shared__ float4 smem4[];
   float2* line = reinterpret_cast<float2*>(smem4) + ri * LS;
   float2* S = f.S + (size_t)(ok ? row : 0) * f.srow;
+  pdl_launch_dependents();
+  pdl_wait();
   float2 v[1][8];
   if (DIR < 0) {
 #pragma unroll
@@ -77,6 +79,8 @@ __global__ void __launch_bounds__(256, 2) kz_fast(const FilmDev* __restrict__ fi
   float2* lines = reinterpret_cast<float2*>(smem4) + qi * LS;   // component c at + c * TQ * LS
   const int gs = TQ * LS;
   const size_t zs = (size_t)ncol;                // S[(c * nz + z) * ncol + q]
+  pdl_launch_dependents();
+  pdl_wait();
   float2 v[3][8];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -133,9 +137,8 @@ cudaError_t y_disp(int dir, const FilmDev* films, const LaunchP& lp, int nunits,
     if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)ky_fast<PY, +1>, a, (int)smem);
     return e;
   }
-  if (dir < 0) ky_fast<PY, -1><<<nunits, threads, smem, s>>>(films, lp);
-  else ky_fast<PY, +1><<<nunits, threads, smem, s>>>(films, lp);
-  return cudaGetLastError();
+  if (dir < 0) return launch_pdl(ky_fast<PY, -1>, nunits, threads, smem, s, films, lp);
+  return launch_pdl(ky_fast<PY, +1>, nunits, threads, smem, s, films, lp);
 }
 
 template <int PZ>
@@ -144,8 +147,7 @@ cudaError_t z_disp(const FilmDev* films, const LaunchP& lp, int nunits, int thre
   if (attr)
     return cudaFuncSetAttribute((const void*)kz_fast<PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
-  kz_fast<PZ><<<nunits, threads, smem, s>>>(films, lp);
-  return cudaGetLastError();
+  return launch_pdl(kz_fast<PZ>, nunits, threads, smem, s, films, lp);
 }
 
 cudaError_t ydispatch(int Py, int dir, const FilmDev* films, const LaunchP& lp, int nunits, int threads,

@@ -33,7 +33,7 @@ __host__ __device__ constexpr int x_tile(int Q) {
 }
 
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+__global__ void __launch_bounds__(256, 3) kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = Q / 8;
   constexpr int TWQ = GRACE_LMAX / (2 * Q);
   constexpr int TY = x_tile(Q);
@@ -59,6 +59,19 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
   const bool demag = (MODE == XM_STEP) || (MODE == XM_ADJ1) || (MODE == XM_ADJ2) ||
                      (MODE == XM_HEFF && (lp.mask & 1u));
   const int nst = 3 * (Q + 1) * TY;
+
+  pdl_launch_dependents();
+  {
+    // this block's rows of m are not written by the previous kernel (y pass)
+    const int rows = 3 * min(TY, ny - y0);
+    const int lines_per_row = (nx * (int)sizeof(float) + 127) / 128;
+    for (int idx = tid; idx < rows * lines_per_row; idx += NT) {
+      const int r = idx / lines_per_row, l = idx - r * lines_per_row;
+      const int c = r / min(TY, ny - y0), t = r - c * min(TY, ny - y0);
+      prefetch_l2(reinterpret_cast<const char*>(m + (size_t)c * f.ncell + (size_t)(z * ny + y0 + t) * nx) + l * 128);
+    }
+  }
+  pdl_wait();
 
   if (demag) {
     // staging S -> shared, TY rows contiguous; loads issued in batches of 8 per thread
@@ -200,13 +213,12 @@ template <int Q>
 cudaError_t launch_q(int mode, const FilmDev* films, const LaunchP& lp, int nunits, int threads,
                      size_t smem, cudaStream_t s) {
   switch (mode) {
-    case XM_R2C: kx_fast<Q, XM_R2C><<<nunits, threads, smem, s>>>(films, lp); break;
-    case XM_HEFF: kx_fast<Q, XM_HEFF><<<nunits, threads, smem, s>>>(films, lp); break;
-    case XM_ADJ1: kx_fast<Q, XM_ADJ1><<<nunits, threads, smem, s>>>(films, lp); break;
-    case XM_ADJ2: kx_fast<Q, XM_ADJ2><<<nunits, threads, smem, s>>>(films, lp); break;
-    default: kx_fast<Q, XM_STEP><<<nunits, threads, smem, s>>>(films, lp); break;
+    case XM_R2C: return launch_pdl(kx_fast<Q, XM_R2C>, nunits, threads, smem, s, films, lp);
+    case XM_HEFF: return launch_pdl(kx_fast<Q, XM_HEFF>, nunits, threads, smem, s, films, lp);
+    case XM_ADJ1: return launch_pdl(kx_fast<Q, XM_ADJ1>, nunits, threads, smem, s, films, lp);
+    case XM_ADJ2: return launch_pdl(kx_fast<Q, XM_ADJ2>, nunits, threads, smem, s, films, lp);
+    default: return launch_pdl(kx_fast<Q, XM_STEP>, nunits, threads, smem, s, films, lp);
   }
-  return cudaGetLastError();
 }
 
 template <int Q>

@@ -15,13 +15,11 @@
 namespace grace {
 namespace {
 
-template <int NZ>
-__device__ __forceinline__ void tensor_product(const float* __restrict__ Tk, int Ky, float sy,
-                                               float2 (&M)[3][NZ], float2 (&H)[3][NZ]) {
-  constexpr int NS = NZ == 1 ? 4 : 6 * NZ - 2;
-  float t[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) t[s] = __ldg(Tk + (size_t)s * Ky);
+// Direct-z tensor product at one (kx, ky): H_a(z) = sum_{z'} sum_b T_ab(kx, ky, z - z') M_b(z'),
+// with the NS slots of this (kx, |ky|) already in t[] and sy the parity sign of ky.
+template <int NZ, int NS>
+__device__ __forceinline__ void tensor_product(const float (&t)[NS], float sy, const float2 (&M)[3][NZ],
+                                               float2 (&H)[3][NZ]) {
 #pragma unroll
   for (int z = 0; z < NZ; ++z) {
     float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
@@ -56,6 +54,21 @@ __device__ __forceinline__ void tensor_product(const float* __restrict__ Tk, int
   }
 }
 
+// Product at one ky held in shared memory (3 NZ lines LS apart from `base`).
+template <int NZ, int NS>
+__device__ __forceinline__ void product_at(float2* base, int LS, const float (&t)[NS], float sy) {
+  float2 M[3][NZ], H[3][NZ];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int zz = 0; zz < NZ; ++zz) M[c][zz] = base[(c * NZ + zz) * LS];
+  tensor_product<NZ, NS>(t, sy, M, H);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int zz = 0; zz < NZ; ++zz) base[(c * NZ + zz) * LS] = H[c][zz];
+}
+
 template <int PY, int NZ>
 __global__ void __launch_bounds__(256, 3) kyz_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = PY / 8;
@@ -79,6 +92,15 @@ __global__ void __launch_bounds__(256, 3) kyz_fast(const FilmDev* __restrict__ f
   const size_t cs = (size_t)NZ * f.Kx * f.srow;        // component stride of S
   const float2* S0 = f.S + ((size_t)z * f.Kx + (ok ? kx : 0)) * f.srow;
 
+  pdl_launch_dependents();
+  {
+    // the tensor slab of this block's kx columns does not depend on the previous kernel
+    const char* t0 = reinterpret_cast<const char*>(f.T + (size_t)kx0 * f.nslot * f.Ky);
+    const int kxn = min(KPB, f.Kx - kx0);
+    const size_t bytes = (size_t)kxn * f.nslot * f.Ky * sizeof(float);
+    for (size_t o = (size_t)tid * 128; o < bytes; o += (size_t)blockDim.x * 128) prefetch_l2(t0 + o);
+  }
+  pdl_wait();
   float2 v[3][8];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -96,25 +118,22 @@ __global__ void __launch_bounds__(256, 3) kyz_fast(const FilmDev* __restrict__ f
     for (int r = 0; r < 8; ++r) lines[c * NZ * LS + pad16(j + r * T)] = v[c][r];
   __syncthreads();
 
-  const int npair = KPB * PY;
-  for (int p = tid; p < npair; p += blockDim.x) {
-    const int ki = p / PY, ky = p - ki * PY;
+  // tensor product: ky and its mirror PY - ky share the tensor slots (parity sign only),
+  // so one thread takes both and loads the slots once
+  constexpr int NSLOT = NZ == 1 ? 4 : 6 * NZ - 2;
+  constexpr int KH = PY / 2 + 1;
+  const int ntask = KPB * KH;
+  for (int p = tid; p < ntask; p += blockDim.x) {
+    const int ki = p / KH, kyp = p - ki * KH;
     const int kxx = kx0 + ki;
     if (kxx >= f.Kx) continue;
-    const bool lo = ky <= PY / 2;
-    const int kyp = lo ? ky : PY - ky;
-    const float sy = lo ? 1.f : -1.f;
-    float2 M[3][NZ], H[3][NZ];
-    float2* base = sm + (size_t)ki * NL * LS + pad16(ky);
+    const float* Tk = f.T + (size_t)kxx * f.nslot * f.Ky + kyp;
+    float t[NSLOT];
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int zz = 0; zz < NZ; ++zz) M[c][zz] = base[(c * NZ + zz) * LS];
-    tensor_product<NZ>(f.T + (size_t)kxx * f.nslot * f.Ky + kyp, f.Ky, sy, M, H);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int zz = 0; zz < NZ; ++zz) base[(c * NZ + zz) * LS] = H[c][zz];
+    for (int s2 = 0; s2 < NSLOT; ++s2) t[s2] = __ldg(Tk + (size_t)s2 * f.Ky);
+    float2* row = sm + (size_t)ki * NL * LS;
+    product_at<NZ, NSLOT>(row + pad16(kyp), LS, t, 1.f);
+    if (kyp > 0 && kyp < PY / 2) product_at<NZ, NSLOT>(row + pad16(PY - kyp), LS, t, -1.f);
   }
   __syncthreads();
 #pragma unroll
@@ -146,8 +165,7 @@ cudaError_t launch_pn(const FilmDev* films, const LaunchP& lp, int nunits, int t
     if (attr_only)
       return cudaFuncSetAttribute((const void*)kyz_fast<PY, NZ>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kyz_fast<PY, NZ><<<nunits, threads, smem, s>>>(films, lp);
-    return cudaGetLastError();
+    return launch_pdl(kyz_fast<PY, NZ>, nunits, threads, smem, s, films, lp);
   } else {
     return cudaErrorInvalidValue;
   }

@@ -41,6 +41,7 @@ struct FilmDev {
   float Ms;                // uniform Ms (A/m)
   float cex;               // 2A/mu0
   float can;               // 2Ku/mu0
+  float cex_ms, can_ms;    // 2A/(mu0 Ms), 2Ku/(mu0 Ms) for the uniform Ms
   float alpha;
   float llg_c;             // -gamma0/(1+alpha^2)
   float hx, hy, hz;        // uniform H_ext (A/m)
@@ -66,6 +67,7 @@ struct LaunchP {
   int RPB;          // rows per block in the split y pass
   int TQ;           // columns per block in the split z pass
   const float2* tw; // twiddle table, GRACE_LMAX entries
+  int pdl;          // launch with programmatic stream serialization
   // adjoint (concatenated films; nullptr when unused)
   const float* mk;          // state to read instead of m[parity] (R2C, ADJ1, ADJ2)
   const float* adj_lam_in;  // lambda_{k+1}
@@ -75,6 +77,32 @@ struct LaunchP {
   float* adj_g_hext;        // += dL/dH_ext (3 N) or nullptr
   float* adj_g_ms;          // += dL/dMs (N) or nullptr
 };
+
+// Programmatic dependent launch: let the next kernel in the stream be scheduled now
+// (it still waits for this grid to finish before reading its results) ...
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+// ... and wait until the previous grid has completed and its writes are visible.  Without
+// a programmatic launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Hint: bring one 128-byte line into L2 (L2 is coherent, so this may precede pdl_wait()).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Launch, with programmatic stream serialization allowed when lp.pdl (see pdl_wait).
+template <typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Args...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t s, const FilmDev* films, const LaunchP& lp) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = lp.pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, films, lp);
+}
 
 // Film owning work unit `unit` of kind `kind` (films sorted by u0[kind]).
 __device__ __forceinline__ int find_film(const FilmDev* __restrict__ films, int nfilms, int kind,
