@@ -137,6 +137,17 @@ bool valid_film(const int n[3], const double cell[3], double Ms, double A, doubl
   return true;
 }
 
+// SMs of the current device (the GB300's 152 when no device is visible, e.g. planning on
+// a host without a GPU).
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+    return n;
+  cudaGetLastError();
+  return 152;
+}
+
 // Tile sizes, unit counts and dynamic shared memory for one group.
 int plan_group(grace_ctx* c, Group& g) {
   int maxQ = 1, maxnx = 1, maxny = 1, maxPy = 1, maxPz = 1;
@@ -152,20 +163,38 @@ int plan_group(grace_ctx* c, Group& g) {
     maxPy = std::max(maxPy, s.P[1]);
     if (s.zfft) maxPz = std::max(maxPz, s.P[2]);
   }
+  // blocks a group launches with a given x tile / kx columns per y block
+  auto xunits = [&](int ty) {
+    long long u = 0;
+    for (int i : g.idx) u += (long long)c->films[i].n[2] * ((c->films[i].n[1] + ty - 1) / ty);
+    return u;
+  };
+  auto yzunits = [&](int kpb) {
+    long long u = 0;
+    for (int i : g.idx) u += (c->classes[c->films[i].cls].Kx + kpb - 1) / kpb;
+    return u;
+  };
+  const long long want = 2LL * sm_count();
+  auto pick_x_tile = [&]() {
+    const int big = fast_x_tile(g.Q);
+    return (big > 1 && xunits(big) < want) ? 1 : big;
+  };
   if (g.split_fast) {
     g.fused = false;
-    g.TY = fast_x_tile(g.Q);
+    g.TY = pick_x_tile();
     g.smem_x = fast_x_smem(g.Q, g.TY);
     g.RPB = fast_y_rows(g.Py);
     g.TQ = fast_z_cols(g.Pz);
     if (g.smem_x > kSmemMax) return GRACE_EUNSUPPORTED;
   } else if (g.fast) {
     g.fused = true;
-    g.TY = fast_x_tile(g.Q);   // compile-time tile of the fast x pass
+    g.TY = pick_x_tile();      // one of the two compile-time tiles of the fast x pass
     g.smem_x = fast_x_smem(g.Q, g.TY);
     const int per = g.nz * (g.Py / 8);
     int KPB = c->tile_yz > 0 ? c->tile_yz : std::max(1, 128 / per);
     while (KPB > 1 && KPB * per > 256) --KPB;
+    if (c->tile_yz <= 0)
+      while (KPB > 1 && yzunits(KPB) < want) KPB /= 2;
     g.KPB = KPB;
     g.smem_yz = fast_yz_smem(g.Py, g.nz, KPB);
     if (g.smem_x > kSmemMax || g.smem_yz > kSmemMax) return GRACE_EUNSUPPORTED;
@@ -520,7 +549,7 @@ cudaError_t configure_all(grace_ctx* c) {
   for (const auto& g : c->groups) {
     cudaError_t e = cudaSuccess;
     if (g.fast) {
-      e = configure_fast_x(g.Q, std::max<size_t>(g.smem_x, 1));
+      e = configure_fast_x(g.Q, g.TY, std::max<size_t>(g.smem_x, 1));
       if (e == cudaSuccess)
         e = g.split_fast ? configure_fast_split(g.Py, g.Pz)
                          : configure_fast_yz(g.Py, g.nz, std::max<size_t>(g.smem_yz, 1));

@@ -32,11 +32,10 @@ __host__ __device__ constexpr int x_tile(int Q) {
   return (256 / (Q / 8)) < 1 ? 1 : ((256 / (Q / 8)) > 4 ? 4 : 256 / (Q / 8));
 }
 
-template <int Q, int MODE>
-__global__ void __launch_bounds__(256, 3) kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+template <int Q, int TY, int MODE>
+__global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = Q / 8;
   constexpr int TWQ = GRACE_LMAX / (2 * Q);
-  constexpr int TY = x_tile(Q);
   constexpr int NT = TY * T;
   constexpr int LS = x_line_stride(Q, TY);
   const int tid = threadIdx.x;
@@ -209,27 +208,48 @@ __global__ void __launch_bounds__(256, 3) kx_fast(const FilmDev* __restrict__ fi
   }
 }
 
-template <int Q>
-cudaError_t launch_q(int mode, const FilmDev* films, const LaunchP& lp, int nunits, int threads,
-                     size_t smem, cudaStream_t s) {
+template <int Q, int TY>
+cudaError_t launch_qt(int mode, const FilmDev* films, const LaunchP& lp, int nunits, size_t smem, cudaStream_t s) {
+  const unsigned threads = TY * (Q / 8);
   switch (mode) {
-    case XM_R2C: return launch_pdl(kx_fast<Q, XM_R2C>, nunits, threads, smem, s, films, lp);
-    case XM_HEFF: return launch_pdl(kx_fast<Q, XM_HEFF>, nunits, threads, smem, s, films, lp);
-    case XM_ADJ1: return launch_pdl(kx_fast<Q, XM_ADJ1>, nunits, threads, smem, s, films, lp);
-    case XM_ADJ2: return launch_pdl(kx_fast<Q, XM_ADJ2>, nunits, threads, smem, s, films, lp);
-    default: return launch_pdl(kx_fast<Q, XM_STEP>, nunits, threads, smem, s, films, lp);
+    case XM_R2C: return launch_pdl(kx_fast<Q, TY, XM_R2C>, nunits, threads, smem, s, films, lp);
+    case XM_HEFF: return launch_pdl(kx_fast<Q, TY, XM_HEFF>, nunits, threads, smem, s, films, lp);
+    case XM_ADJ1: return launch_pdl(kx_fast<Q, TY, XM_ADJ1>, nunits, threads, smem, s, films, lp);
+    case XM_ADJ2: return launch_pdl(kx_fast<Q, TY, XM_ADJ2>, nunits, threads, smem, s, films, lp);
+    default: return launch_pdl(kx_fast<Q, TY, XM_STEP>, nunits, threads, smem, s, films, lp);
   }
 }
 
-template <int Q>
-cudaError_t attr_q(size_t smem) {
+template <int Q, int TY>
+cudaError_t attr_qt(size_t smem) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_R2C>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_HEFF>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_STEP>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_ADJ1>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, XM_ADJ2>, a, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_R2C>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_HEFF>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_STEP>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_ADJ1>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_ADJ2>, a, (int)smem);
   return e;
+}
+
+// Two tiles per length: the large one (x_tile(Q) lines) and one line per block, for
+// groups too small to fill the GPU with large tiles.
+template <int Q>
+cudaError_t launch_q(int mode, int TY, const FilmDev* films, const LaunchP& lp, int nunits, size_t smem,
+                     cudaStream_t s) {
+  if constexpr (x_tile(Q) > 1) {
+    if (TY == x_tile(Q)) return launch_qt<Q, x_tile(Q)>(mode, films, lp, nunits, smem, s);
+  }
+  if (TY == 1) return launch_qt<Q, 1>(mode, films, lp, nunits, smem, s);
+  return cudaErrorInvalidValue;
+}
+
+template <int Q>
+cudaError_t attr_q(int TY, size_t smem) {
+  if constexpr (x_tile(Q) > 1) {
+    if (TY == x_tile(Q)) return attr_qt<Q, x_tile(Q)>(smem);
+  }
+  if (TY == 1) return attr_qt<Q, 1>(smem);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -242,17 +262,17 @@ size_t fast_x_smem(int Q, int TY) {
   return (size_t)3 * TY * x_line_stride(Q, TY) * sizeof(float2) + (size_t)3 * TY * Q * sizeof(float);
 }
 
-cudaError_t configure_fast_x(int Q, size_t smem) {
+cudaError_t configure_fast_x(int Q, int TY, size_t smem) {
   switch (Q) {
-    case 8: return attr_q<8>(smem);
-    case 16: return attr_q<16>(smem);
-    case 32: return attr_q<32>(smem);
-    case 64: return attr_q<64>(smem);
-    case 128: return attr_q<128>(smem);
-    case 256: return attr_q<256>(smem);
-    case 512: return attr_q<512>(smem);
-    case 1024: return attr_q<1024>(smem);
-    case 2048: return attr_q<2048>(smem);
+    case 8: return attr_q<8>(TY, smem);
+    case 16: return attr_q<16>(TY, smem);
+    case 32: return attr_q<32>(TY, smem);
+    case 64: return attr_q<64>(TY, smem);
+    case 128: return attr_q<128>(TY, smem);
+    case 256: return attr_q<256>(TY, smem);
+    case 512: return attr_q<512>(TY, smem);
+    case 1024: return attr_q<1024>(TY, smem);
+    case 2048: return attr_q<2048>(TY, smem);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -260,17 +280,16 @@ cudaError_t configure_fast_x(int Q, size_t smem) {
 cudaError_t launch_fast_x(int Q, int mode, const FilmDev* films, const LaunchP& lp, int nunits, int TY,
                           size_t smem, cudaStream_t s) {
   if (nunits <= 0) return cudaSuccess;
-  const int threads = TY * (Q / 8);
   switch (Q) {
-    case 8: return launch_q<8>(mode, films, lp, nunits, threads, smem, s);
-    case 16: return launch_q<16>(mode, films, lp, nunits, threads, smem, s);
-    case 32: return launch_q<32>(mode, films, lp, nunits, threads, smem, s);
-    case 64: return launch_q<64>(mode, films, lp, nunits, threads, smem, s);
-    case 128: return launch_q<128>(mode, films, lp, nunits, threads, smem, s);
-    case 256: return launch_q<256>(mode, films, lp, nunits, threads, smem, s);
-    case 512: return launch_q<512>(mode, films, lp, nunits, threads, smem, s);
-    case 1024: return launch_q<1024>(mode, films, lp, nunits, threads, smem, s);
-    case 2048: return launch_q<2048>(mode, films, lp, nunits, threads, smem, s);
+    case 8: return launch_q<8>(mode, TY, films, lp, nunits, smem, s);
+    case 16: return launch_q<16>(mode, TY, films, lp, nunits, smem, s);
+    case 32: return launch_q<32>(mode, TY, films, lp, nunits, smem, s);
+    case 64: return launch_q<64>(mode, TY, films, lp, nunits, smem, s);
+    case 128: return launch_q<128>(mode, TY, films, lp, nunits, smem, s);
+    case 256: return launch_q<256>(mode, TY, films, lp, nunits, smem, s);
+    case 512: return launch_q<512>(mode, TY, films, lp, nunits, smem, s);
+    case 1024: return launch_q<1024>(mode, TY, films, lp, nunits, smem, s);
+    case 2048: return launch_q<2048>(mode, TY, films, lp, nunits, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

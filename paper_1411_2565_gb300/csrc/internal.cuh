@@ -130,7 +130,7 @@ cudaError_t launch_energy(const FilmDev* films, const LaunchP& lp, const float* 
 bool fast_x_supported(int Q);
 int fast_x_tile(int Q);
 size_t fast_x_smem(int Q, int TY);
-cudaError_t configure_fast_x(int Q, size_t smem);
+cudaError_t configure_fast_x(int Q, int TY, size_t smem);
 cudaError_t launch_fast_x(int Q, int mode, const FilmDev* films, const LaunchP& lp, int nunits, int TY,
                           size_t smem, cudaStream_t s);
 bool fast_yz_supported(int Py, int nz);
