@@ -170,13 +170,19 @@ def _sampled_cells(grid, rng_seed):
     return fixed + rand
 
 
-@pytest.mark.parametrize("name", ["film_large", "block"])
-def test_full_size_sampled_cells(name):
+@pytest.mark.parametrize("name,after", [("film_large", 0), ("film_large", 100), ("film_large", 1000),
+                                        ("block", 0), ("block", 100)])
+def test_full_size_sampled_cells(name, after):
     """Full-size workloads in the launch configuration the benchmark times: H_eff and one
-    Euler step at sampled cells against the oracle's direct demag sum at those cells."""
+    Euler step at sampled cells against the oracle's direct demag sum at those cells, at
+    the start and after `after` GPU steps with the oracle fed the GPU's state (random
+    starts diverge chaotically between FP32 and FP64, so trajectories are not compared)."""
     w = getattr(workloads, name)()
     f, m0 = w.films[0], w.m0[0]
     g = make(f, m0)
+    if after:
+        g.step(after, w.dt)
+        m0 = g.get_m().cpu().numpy().reshape(m0.shape)
     h = g.heff().cpu().numpy().reshape(m0.shape)
     cells = _sampled_cells(f.grid, 77)
     p = params(f)
@@ -196,3 +202,38 @@ def test_full_size_sampled_cells(name):
         assert np.abs(m1[:, z, y, x] - ref).max() <= 2e-6
     n = np.sqrt((m1.astype(np.float64) ** 2).sum(0))
     assert np.abs(n - 1).max() <= 1e-6
+
+
+def test_ensemble_films_full_trajectory():
+    """One film of each ensemble size class (64x16x1, 128x32x1, 256x64x2, 200x50x1) stepped
+    together for the full 2000 steps: per-film <m> within 1e-4 of the oracle."""
+    _, GraceBatch = _grace()
+    w = workloads.ensemble(nfilms=64, seed=4)
+    picked, seen = [], set()
+    for k, f in enumerate(w.films):
+        if f.grid not in seen:
+            seen.add(f.grid)
+            picked.append(k)
+    films = [w.films[k] for k in picked]
+    m0s = [w.m0[k] for k in picked]
+    gb = GraceBatch(films, device=DEV)
+    gb.set_m(torch.from_numpy(np.concatenate([m.reshape(-1) for m in m0s])).to(DEV))
+    gb.step(w.steps, w.dt)
+    parts = gb.split(gb.get_m())
+    for f, m0, mg in zip(films, m0s, parts):
+        mo = llg.run(m0, params(f), w.dt, w.steps)
+        d = np.abs(mg.cpu().numpy().reshape(3, -1).mean(1) - mo.reshape(3, -1).mean(1)).max()
+        assert d <= 1e-4, (f.grid, d)
+
+
+def test_adjoint_film_forward_4096_steps():
+    """The 256x64x2 adjoint film (per-cell Ms) forward for its full 4096 steps: <m> within
+    1e-4 of the oracle."""
+    w = workloads.adjoint_film()
+    f, m0 = w.films[0], w.m0[0]
+    g = make(f, m0, ms=w.ms_field)
+    g.step(w.steps, w.dt)
+    mg = g.get_m().cpu().numpy().reshape(m0.shape)
+    mo = llg.run(m0, params(f, ms=w.ms_field), w.dt, w.steps)
+    d = np.abs(mg.reshape(3, -1).mean(1) - mo.reshape(3, -1).mean(1)).max()
+    assert d <= 1e-4, d
