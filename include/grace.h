@@ -63,7 +63,9 @@ enum {
 enum {
   GRACE_OPT_GRAPH = 1,        /* 1 (default): grace_step replays captured CUDA graphs; 0: plain launches */
   GRACE_OPT_GRAPH_STEPS = 2,  /* steps per captured graph (even, >= 2; default 16) */
-  GRACE_OPT_TILE_X = 3,       /* y lines per x-pass block (0 = automatic); before grace_bind only */
+  GRACE_OPT_TILE_X = 3,       /* y lines per x-pass block (0 = automatic; with compile-time FFT
+                                 lengths 1 selects one line, >1 the larger compiled tile);
+                                 before grace_bind only */
   GRACE_OPT_TILE_YZ = 4,      /* kx columns per fused y-z block (0 = automatic); before grace_bind only */
   GRACE_OPT_PDL = 5           /* 1 (default): consecutive kernels use programmatic dependent launch */
 };

@@ -1,0 +1,114 @@
+"""Autotuner for the launch schedule of a film or an ensemble.
+
+For a given set of films it times each candidate schedule — x-pass tile (one line per
+block or the larger compiled tile), kx columns per fused y block, steps per captured CUDA
+graph and programmatic dependent launch — on the real device with CUDA events and keeps
+the fastest.  Results are cached in a JSON file keyed by the film shapes and the device
+name, so a later ``Grace(..., options=autotune.best(...))`` reuses them without timing.
+"""
+from __future__ import annotations
+
+import hashlib
+import itertools
+import json
+import os
+from typing import Dict, List, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+
+CACHE = os.environ.get("GRACE_AUTOTUNE_CACHE",
+                       os.path.join(os.path.expanduser("~"), ".cache", "grace_gb300_autotune.json"))
+# schedules tuned on a GB300 for the benchmark shapes, shipped with the package
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.json")
+
+CANDIDATES = {
+    _lib.OPT_TILE_X: (0, 1, 2),
+    _lib.OPT_TILE_YZ: (0, 1, 2, 4),
+    _lib.OPT_GRAPH_STEPS: (8, 16, 32),
+    _lib.OPT_PDL: (0, 1),
+}
+BIND_OPTIONS = (_lib.OPT_TILE_X, _lib.OPT_TILE_YZ)
+
+
+def _key(films, device) -> str:
+    shapes = sorted(f"{f.grid}|{f.cell}" for f in films)
+    name = torch.cuda.get_device_name(device)
+    return hashlib.sha256(("|".join(shapes) + "|" + name).encode()).hexdigest()[:24]
+
+
+def _load() -> Dict:
+    if os.path.exists(CACHE):
+        with open(CACHE) as fh:
+            return json.load(fh)
+    return {}
+
+
+def _store(d: Dict):
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    tmp = CACHE + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(d, fh, indent=1)
+    os.replace(tmp, CACHE)
+
+
+def _time(films, m0s, dt, options, device, steps=64, reps=3) -> float:
+    from .grace import Grace, GraceBatch
+    bind = {k: v for k, v in options.items() if k in BIND_OPTIONS}
+    if len(films) == 1:
+        f = films[0]
+        g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=device, options=bind)
+        g.set_hext(f.hext)
+    else:
+        g = GraceBatch(films, device=device, options=bind)
+    for k, v in options.items():
+        if k not in BIND_OPTIONS:
+            g.set_option(k, v)
+    g.set_m(torch.from_numpy(np.concatenate([m.reshape(-1) for m in m0s])).to(device))
+    g.step(steps, dt)
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.step(steps, dt)
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b) / steps)
+    g.close()
+    return best
+
+
+def tune(films: Sequence, m0s: Sequence[np.ndarray], dt: float, device="cuda", force=False) -> Dict[int, int]:
+    """Time every candidate schedule for these films; returns and caches the best options."""
+    device = torch.device(device)
+    cache = _load()
+    key = _key(films, device)
+    if key in cache and not force:
+        return {int(k): v for k, v in cache[key]["options"].items()}
+    results = []
+    names = list(CANDIDATES)
+    for values in itertools.product(*(CANDIDATES[n] for n in names)):
+        opts = dict(zip(names, values))
+        try:
+            ms = _time(films, m0s, dt, opts, device)
+        except _lib.GraceError:
+            continue                       # a tile this shape does not support
+        results.append((ms, opts))
+    results.sort(key=lambda r: r[0])
+    best_ms, best = results[0]
+    cache[key] = {"options": {str(k): v for k, v in best.items()}, "ms_per_step": best_ms,
+                  "films": len(films), "tried": len(results)}
+    _store(cache)
+    return best
+
+
+def best(films: Sequence, device="cuda") -> Dict[int, int]:
+    """Cached options for these films: the local cache, else the shipped GB300 table, else {}."""
+    key = _key(films, torch.device(device))
+    entry = _load().get(key)
+    if entry is None and os.path.exists(SHIPPED):
+        with open(SHIPPED) as fh:
+            entry = json.load(fh).get(key)
+    return {} if entry is None else {int(k): v for k, v in entry["options"].items()}

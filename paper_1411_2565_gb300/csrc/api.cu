@@ -177,6 +177,8 @@ int plan_group(grace_ctx* c, Group& g) {
   const long long want = 2LL * sm_count();
   auto pick_x_tile = [&]() {
     const int big = fast_x_tile(g.Q);
+    if (c->tile_x == 1) return 1;                 // explicit: one line per block
+    if (c->tile_x > 1) return big;                // explicit: the large compiled tile
     return (big > 1 && xunits(big) < want) ? 1 : big;
   };
   if (g.split_fast) {

@@ -1,0 +1,35 @@
+"""Autotuner: every schedule it may pick computes the same result (schedules change the
+grouping of work into blocks, not the arithmetic of a line)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from paper_1411_2565_gb300 import _lib
+from paper_1411_2565_gb300 import build as libbuild
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tuned_schedule_reproduces_default(tmp_path, monkeypatch):
+    libbuild.build()
+    from paper_1411_2565_gb300 import autotune
+    from paper_1411_2565_gb300.grace import Grace
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "cache.json"))
+    w = workloads.film_small()
+    f, m0 = w.films[0], w.m0[0]
+    opts = autotune.tune([f], [m0], w.dt)
+    assert set(opts) == set(autotune.CANDIDATES)
+    assert autotune.best([f]) == opts                      # cached
+    md = torch.from_numpy(m0.reshape(-1)).cuda()
+    ref = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0)
+    ref.set_m(md)
+    ref.step(40, w.dt)
+    for o in ({_lib.OPT_TILE_X: 1, _lib.OPT_TILE_YZ: 1}, {_lib.OPT_TILE_X: 2, _lib.OPT_TILE_YZ: 4},
+              opts):
+        g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, options=o)
+        g.set_m(md)
+        g.step(40, w.dt)
+        assert torch.equal(g.get_m(), ref.get_m()), o
