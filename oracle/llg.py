@@ -128,15 +128,28 @@ def euler_step(m, p: Params, dt: float, demag: Optional[Demag] = None):
     return normalise(m + dt * llg_rhs(m, heff(m, p, demag), p.alpha, p.gamma0))
 
 
-def run(m0, p: Params, dt: float, steps: int, demag: Optional[Demag] = None, keep=False):
-    """Take ``steps`` Euler steps; returns the final state (and every state if ``keep``)."""
+def heun_step(m, p: Params, dt: float, demag: Optional[Demag] = None):
+    """Explicit trapezoid (Heun) with renormalisation, the higher-order integrator the paper
+    names as future work (Sec. 6): k1 = f(m_n), m* = normalise(m_n + dt k1),
+    k2 = f(m*), m_{n+1} = normalise(m_n + dt (k1 + k2)/2)."""
+    m = np.asarray(m, dtype=np.float64)
+    k1 = llg_rhs(m, heff(m, p, demag), p.alpha, p.gamma0)
+    ms = normalise(m + dt * k1)
+    k2 = llg_rhs(ms, heff(ms, p, demag), p.alpha, p.gamma0)
+    return normalise(m + 0.5 * dt * (k1 + k2))
+
+
+def run(m0, p: Params, dt: float, steps: int, demag: Optional[Demag] = None, keep=False,
+        integrator: str = "euler"):
+    """Take ``steps`` steps (Euler or Heun); returns the final state (and every state if ``keep``)."""
     m = np.asarray(m0, dtype=np.float64)
     if demag is None:
         _, nz, ny, nx = m.shape
         demag = Demag((nx, ny, nz), p.cell, "fft", p.r_switch)
+    step = heun_step if integrator == "heun" else euler_step
     states = [m] if keep else None
     for _ in range(steps):
-        m = euler_step(m, p, dt, demag)
+        m = step(m, p, dt, demag)
         if keep:
             states.append(m)
     return (m, states) if keep else m
