@@ -67,7 +67,12 @@ enum {
                                  lengths 1 selects one line, >1 the larger compiled tile);
                                  before grace_bind only */
   GRACE_OPT_TILE_YZ = 4,      /* kx columns per fused y-z block (0 = automatic); before grace_bind only */
-  GRACE_OPT_PDL = 5           /* 1 (default): consecutive kernels use programmatic dependent launch */
+  GRACE_OPT_PDL = 5,          /* 1 (default): consecutive kernels use programmatic dependent launch */
+  GRACE_OPT_INTEGRATOR = 6    /* 0 (default): explicit Euler (Sec. 3); 1: Heun, the explicit
+                                 trapezoid m* = normalise(m + dt f(m)),
+                                 m' = normalise(m + dt (f(m) + f(m*))/2), a higher-order
+                                 integrator named as future work in Sec. 6 (two H_eff per step;
+                                 grace_backward supports Euler only) */
 };
 
 /* Kernel kinds reported by grace_trace_read. */
@@ -145,7 +150,8 @@ int grace_set_ms_field(grace_ctx *ctx, const float *dev_ms);
  */
 int grace_heff(grace_ctx *ctx, float *dev_h, unsigned term_mask);
 
-/* grace_step - n explicit Euler steps of Eq. 3 with renormalisation, time step dt_s. */
+/* grace_step - n time steps of Eq. 3 with renormalisation, time step dt_s: explicit Euler,
+ * or Heun when GRACE_OPT_INTEGRATOR is 1. */
 int grace_step(grace_ctx *ctx, int n, double dt_s);
 
 /*

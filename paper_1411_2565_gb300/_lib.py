@@ -12,7 +12,7 @@ STATUS = {0: "GRACE_OK", -1: "GRACE_EINVAL", -2: "GRACE_EWORKSPACE", -3: "GRACE_
           -4: "GRACE_ETIMEOUT", -5: "GRACE_ESTATE", -6: "GRACE_ENONFINITE",
           -7: "GRACE_EUNSUPPORTED"}
 TERM_DEMAG, TERM_EXCH, TERM_ANIS, TERM_ZEEMAN, TERM_ALL = 1, 2, 4, 8, 15
-OPT_GRAPH, OPT_GRAPH_STEPS, OPT_TILE_X, OPT_TILE_YZ, OPT_PDL = 1, 2, 3, 4, 5
+OPT_GRAPH, OPT_GRAPH_STEPS, OPT_TILE_X, OPT_TILE_YZ, OPT_PDL, OPT_INTEGRATOR = 1, 2, 3, 4, 5, 6
 KERNEL_NAMES = ("yz_fast", "x_fast", "yz", "y", "z", "x", "y_fast", "z_fast")
 
 _P = C.c_void_p

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrace.so")
-SOURCES = ["api.cu", "hotpath.cu", "tensor.cu", "fastx.cu", "fastyz.cu", "fastsplit.cu", "noalloc.cu"]
+SOURCES = ["fastx_q1024.cu", "fastx_q512.cu", "fastx_q128.cu", "fastx_q8.cu", "fastyz.cu", "fastsplit.cu",
+           "api.cu", "hotpath.cu", "tensor.cu", "fastx.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -76,7 +76,7 @@ struct grace_ctx {
   std::vector<int> film_group;
   long long ncell = 0;
   int tile_x = 0, tile_yz = 0;      // 0 = automatic
-  size_t o_tw = 0, o_films = 0, o_run = 0, o_m0 = 0, o_m1 = 0, o_H = 0, o_part = 0, o_eout = 0;
+  size_t o_tw = 0, o_films = 0, o_run = 0, o_m0 = 0, o_m1 = 0, o_H = 0, o_k1 = 0, o_part = 0, o_eout = 0;
   std::vector<size_t> o_S;
   size_t run_bytes = 0, build_bytes = 0, need = 0;
   char* ws = nullptr;
@@ -88,6 +88,7 @@ struct grace_ctx {
   const float* h_field = nullptr;
   bool use_graph = true;
   bool pdl = true;
+  int integrator = 0;               // 0: explicit Euler, 1: Heun
   int graph_steps = 16;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -390,6 +391,8 @@ int plan(grace_ctx* c) {
   r += mbytes;
   c->o_H = r;
   r += mbytes;
+  c->o_k1 = r;
+  r += mbytes;
   c->o_part = r;
   r = al256(r + (size_t)kEnergyBlocks * 8 * sizeof(double));
   c->o_eout = r;
@@ -448,6 +451,7 @@ LaunchP group_lp(const grace_ctx* c, const Group& g) {
   lp.TQ = g.TQ;
   lp.tw = reinterpret_cast<const float2*>(c->ws + c->o_tw);
   lp.pdl = c->pdl ? 1 : 0;
+  lp.k1 = reinterpret_cast<float*>(c->ws + c->o_run + c->o_k1);
   return lp;
 }
 
@@ -509,6 +513,9 @@ cudaError_t enqueue_x(grace_ctx* c, const Group& g, int mode, const LaunchP& lp,
   return cudaSuccess;
 }
 
+// One time step from the state in buffer `parity`.  Euler leaves the new state in the other
+// buffer; Heun (predictor into the other buffer, corrector back into this one) leaves it in
+// the same buffer.
 cudaError_t enqueue_step(grace_ctx* c, int parity, float dt, cudaStream_t s) {
   for (const auto& g : c->groups) {
     LaunchP lp = group_lp(c, g);
@@ -516,11 +523,23 @@ cudaError_t enqueue_step(grace_ctx* c, int parity, float dt, cudaStream_t s) {
     lp.dt = dt;
     cudaError_t e = enqueue_conv(c, g, lp, s);
     if (e != cudaSuccess) return e;
-    e = enqueue_x(c, g, XM_STEP, lp, s);
+    if (c->integrator == 1) {
+      e = enqueue_x(c, g, XM_HEUN1, lp, s);
+      if (e != cudaSuccess) return e;
+      e = enqueue_conv(c, g, lp, s);
+      if (e != cudaSuccess) return e;
+      LaunchP lp2 = lp;
+      lp2.parity = parity ^ 1;
+      e = enqueue_x(c, g, XM_HEUN2, lp2, s);
+    } else {
+      e = enqueue_x(c, g, XM_STEP, lp, s);
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
+
+int parity_flip(const grace_ctx* c) { return c->integrator == 1 ? 0 : 1; }
 
 cudaError_t enqueue_r2c(grace_ctx* c) {
   for (const auto& g : c->groups) {
@@ -835,7 +854,8 @@ int grace_step(grace_ctx* c, int n, double dt) {
       // inside a graph plain serialisation measured faster than programmatic edges
       const bool pdl = c->pdl;
       c->pdl = false;
-      for (int s = 0; s < G && e == cudaSuccess; ++s) e = enqueue_step(c, (p + s) & 1, fdt, c->cap);
+      for (int s = 0; s < G && e == cudaSuccess; ++s)
+        e = enqueue_step(c, (p + s * parity_flip(c)) & 1, fdt, c->cap);
       c->pdl = pdl;
       cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
       if (e != cudaSuccess) {
@@ -855,7 +875,7 @@ int grace_step(grace_ctx* c, int n, double dt) {
   }
   for (; done < n; ++done) {
     GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, c->stream));
-    c->parity ^= 1;
+    c->parity ^= parity_flip(c);
   }
   return GRACE_OK;
 }
@@ -920,6 +940,7 @@ int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt
   int st = ready(c, true);
   if (st) return st;
   if (!dL_dmT) return fail(c, GRACE_EINVAL, "dL/dm_T pointer is NULL");
+  if (c->integrator != 0) return fail(c, GRACE_EUNSUPPORTED, "the adjoint is built for the Euler integrator");
   if (n < 0 || ckpt < 1) return fail(c, GRACE_EINVAL, "n must be >= 0 and ckpt_every >= 1");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GRACE_EINVAL, "dt must be positive");
   size_t need = 0;
@@ -1007,6 +1028,11 @@ int grace_set_option(grace_ctx* c, int option, long long value) {
     case GRACE_OPT_PDL:
       if (value != 0 && value != 1) return fail(c, GRACE_EINVAL, "GRACE_OPT_PDL takes 0 or 1");
       c->pdl = value != 0;
+      drop_graphs(c);
+      return GRACE_OK;
+    case GRACE_OPT_INTEGRATOR:
+      if (value != 0 && value != 1) return fail(c, GRACE_EINVAL, "GRACE_OPT_INTEGRATOR takes 0 or 1");
+      c->integrator = (int)value;
       drop_graphs(c);
       return GRACE_OK;
     case GRACE_OPT_TILE_X:

@@ -102,15 +102,32 @@ __device__ __forceinline__ float3 cell_apply(const FilmDev& f, const LaunchP& lp
   const float mx = c.mx, my = c.my, mz = c.mz;
   const float3 p = cross3(mx, my, mz, c.hx, c.hy, c.hz);
   const float3 q = cross3(mx, my, mz, p.x, p.y, p.z);
-  const float cdt = f.llg_c * lp.dt;
-  float ux = fmaf(cdt, fmaf(f.alpha, q.x, p.x), mx);
-  float uy = fmaf(cdt, fmaf(f.alpha, q.y, p.y), my);
-  float uz = fmaf(cdt, fmaf(f.alpha, q.z, p.z), mz);
+  float* mo = lp.parity ? f.m0 : f.m1;
+  float ux, uy, uz;
+  if (MODE == XM_HEUN2) {
+    // corrector: m_{n+1} = normalise(m_n + dt (k1 + k2)/2), k2 = f(m*) with m* the current
+    // state; m_n sits in the output buffer (each cell reads only its own entry there)
+    const float* k1 = lp.k1 + 3 * f.cell0;
+    const float hdt = 0.5f * f.llg_c * lp.dt;
+    ux = fmaf(hdt, fmaf(f.alpha, q.x, p.x), fmaf(0.5f * lp.dt, k1[i], mo[i]));
+    uy = fmaf(hdt, fmaf(f.alpha, q.y, p.y), fmaf(0.5f * lp.dt, k1[N + i], mo[N + i]));
+    uz = fmaf(hdt, fmaf(f.alpha, q.z, p.z), fmaf(0.5f * lp.dt, k1[2 * N + i], mo[2 * N + i]));
+  } else {
+    const float cdt = f.llg_c * lp.dt;
+    if (MODE == XM_HEUN1) {
+      float* k1 = lp.k1 + 3 * f.cell0;
+      k1[i] = f.llg_c * fmaf(f.alpha, q.x, p.x);
+      k1[N + i] = f.llg_c * fmaf(f.alpha, q.y, p.y);
+      k1[2 * N + i] = f.llg_c * fmaf(f.alpha, q.z, p.z);
+    }
+    ux = fmaf(cdt, fmaf(f.alpha, q.x, p.x), mx);
+    uy = fmaf(cdt, fmaf(f.alpha, q.y, p.y), my);
+    uz = fmaf(cdt, fmaf(f.alpha, q.z, p.z), mz);
+  }
   const float inv = rnorm(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
   ux *= inv;
   uy *= inv;
   uz *= inv;
-  float* mo = lp.parity ? f.m0 : f.m1;
   mo[i] = ux;
   mo[N + i] = uy;
   mo[2 * N + i] = uz;

@@ -1,0 +1,263 @@
+// Fused x pass for films whose x transform has compile-time length Q = Px/2 >= 8.
+//
+// Block = TY consecutive y lines of one z plane, Q/8 threads per line (thread (ty, j),
+// ty fastest so that TY neighbouring rows of S are read and written together).
+// Per field component the x C2R runs in registers: thread j ends holding
+// y[j + s Q/8] = H(2n) + i H(2n+1), n = j + s Q/8, i.e. H at cells x = 2n, 2n+1 for
+// s < 4.  Those are exactly the cells whose new magnetisation forms its input
+// z[j + s Q/8] = M(2n) + i M(2n+1) to the forward transform, so C2R -> H_eff ->
+// Euler step (Eq. 3, renormalised) -> R2C never leaves registers; shared memory only
+// stages the spectrum for the Hermitian merge/split and carries the FFT exchanges.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "cell.cuh"
+#include "fftreg.cuh"
+#include "internal.cuh"
+
+namespace grace {
+namespace fastx {
+
+// Line-buffer stride for TY y lines of 3 components (line (t, c) at (3 t + c) * LS):
+// the staging and store loops run t fastest, so 3 LS must put the TY lines of one k on
+// different bank pairs; the FFT exchanges run j fastest within one line.
+__host__ __device__ constexpr int x_line_stride(int Q, int TY) {
+  return fast_line_stride(Q, TY >= 4 ? 12 : (TY == 2 ? 8 : 0));
+}
+
+// Shared memory: 3 TY line buffers (x_line_stride float2 each) for staging, the Hermitian
+// merge / split and the FFT exchanges, then hs[3][TY][Q] floats holding H_demag per cell
+// and, after the update, Ms m of the new state.
+// y lines per block: 256 threads where the line allows, at most 4 lines
+__host__ __device__ constexpr int x_tile(int Q) {
+  return (256 / (Q / 8)) < 1 ? 1 : ((256 / (Q / 8)) > 4 ? 4 : 256 / (Q / 8));
+}
+
+template <int Q, int TY, int MODE>
+__global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+  constexpr int T = Q / 8;
+  constexpr int TWQ = GRACE_LMAX / (2 * Q);
+  constexpr int NT = TY * T;
+  constexpr int LS = x_line_stride(Q, TY);
+  const int tid = threadIdx.x;
+  const int j = tid % T, ty = tid / T;
+  const int unit = blockIdx.x;
+  const FilmDev& f = films[find_film(films, lp.nfilms, UK_X, unit)];
+  const int nx = f.nx, ny = f.ny, nz = f.nz;
+  const int nyt = (ny + TY - 1) / TY;
+  const int local = unit - f.u0[UK_X];
+  const int z = local / nyt;
+  const int y0 = (local - z * nyt) * TY;
+  extern __shared__ float4 smem4[];
+  float2* sm = reinterpret_cast<float2*>(smem4);
+  float2* lines = sm + 3 * ty * LS;                              // this thread's 3 lines
+  float* hs = reinterpret_cast<float*>(sm + 3 * TY * LS);        // [3][TY][Q]
+  const float* __restrict__ m = lp.mk ? lp.mk + 3 * f.cell0 : (lp.parity ? f.m1 : f.m0);
+  const size_t srow = f.srow;
+  const size_t sc = (size_t)nz * f.Kx * srow;                    // component stride of S
+  float2* Sz = f.S + (size_t)z * f.Kx * srow;                    // S[c=0][z][.][.]
+  const bool demag = (MODE == XM_STEP) || (MODE == XM_ADJ1) || (MODE == XM_ADJ2) ||
+                     (MODE == XM_HEUN1) || (MODE == XM_HEUN2) ||
+                     (MODE == XM_HEFF && (lp.mask & 1u));
+  const int nst = 3 * (Q + 1) * TY;
+
+  pdl_launch_dependents();
+  {
+    // this block's rows of m are not written by the previous kernel (y pass)
+    const int rows = 3 * min(TY, ny - y0);
+    const int lines_per_row = (nx * (int)sizeof(float) + 127) / 128;
+    for (int idx = tid; idx < rows * lines_per_row; idx += NT) {
+      const int r = idx / lines_per_row, l = idx - r * lines_per_row;
+      const int c = r / min(TY, ny - y0), t = r - c * min(TY, ny - y0);
+      prefetch_l2(reinterpret_cast<const char*>(m + (size_t)c * f.ncell + (size_t)(z * ny + y0 + t) * nx) + l * 128);
+    }
+  }
+  pdl_wait();
+
+  if (demag) {
+    // staging S -> shared, TY rows contiguous; loads issued in batches of 8 per thread
+    constexpr int U = 8;
+    for (int base = 0; base < nst; base += U * NT) {
+      float2 buf[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT + tid;
+        const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
+        buf[u] = (idx < nst && y0 + t < ny) ? Sz[c * sc + (size_t)k * srow + y0 + t]
+                                             : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT + tid;
+        const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
+        if (idx < nst) sm[(3 * t + c) * LS + pad16(k)] = buf[u];
+      }
+    }
+    __syncthreads();
+    float2 v[3][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      // C_k = (X_k + conj X_{Q-k}) + i W^{-k} (X_k - conj X_{Q-k})
+      const int k = j + r * T;
+      const float2 w = cconj(__ldg(lp.tw + k * TWQ));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 xk = lines[c * LS + pad16(k)], xq = lines[c * LS + pad16(Q - k)];
+        const float2 a = cadd(xk, cconj(xq)), b = csub(xk, cconj(xq));
+        const float2 wb = cmul(w, b);
+        v[c][r] = make_float2(a.x - wb.y, a.y + wb.x);
+      }
+    }
+    __syncthreads();
+    fft_reg<Q, +1, false, 3>(v, j, lines, LS, lp.tw);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2* h2 = reinterpret_cast<float2*>(hs + (c * TY + ty) * Q);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) h2[j + s * T] = v[c][s];     // H at cells 2n, 2n+1
+    }
+  } else {
+    for (int idx = tid; idx < 3 * TY * Q; idx += NT) hs[idx] = 0.f;
+  }
+  __syncthreads();
+
+  if constexpr (MODE == XM_ADJ1 || MODE == XM_ADJ2) {
+    // adjoint halves: H_demag(m_k) -> lambda_part, nu (R2C of nu follows), or D(nu) -> lambda_k
+    for (int idx = tid; idx < TY * Q; idx += NT) {
+      const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+      float* hp = hs + t * Q + x;
+      float3 r = make_float3(0.f, 0.f, 0.f);
+      if (x < nx && y < ny) {
+        const int i = (z * ny + y) * nx + x;
+        if (MODE == XM_ADJ1) r = adj1_cell(f, lp, m, i, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q]);
+        else adj2_cell(f, lp, m, i, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q]);
+      }
+      hp[0] = r.x;
+      hp[TY * Q] = r.y;
+      hp[2 * TY * Q] = r.z;
+    }
+  } else {
+  // cell update, one thread per cell of the TY x Q tile (x >= nx, y >= ny give zeros);
+  // each thread owns 8 cells and issues the loads of 4 of them before using any
+    const unsigned mask =
+        (MODE == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
+    constexpr int U = 4;
+    for (int base = 0; base < TY * Q; base += U * NT) {
+      CellState cs[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT + tid;
+        const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+        ok[u] = idx < TY * Q && x < nx && y < ny;
+        if (ok[u]) {
+          const float* hp = hs + t * Q + x;
+          cs[u] = cell_field(f, mask, m, (z * ny + y) * nx + x, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * NT + tid;
+        if (idx >= TY * Q) continue;
+        const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+        float3 r = make_float3(0.f, 0.f, 0.f);
+        if (ok[u]) r = cell_apply<MODE>(f, lp, (z * ny + y) * nx + x, cs[u]);
+        float* hp = hs + t * Q + x;
+        hp[0] = r.x;
+        hp[TY * Q] = r.y;
+        hp[2 * TY * Q] = r.z;
+      }
+    }
+  }
+  const bool r2c = (MODE != XM_HEFF && MODE != XM_ADJ2) || (MODE == XM_HEFF && demag);
+  if (!r2c) return;
+  __syncthreads();
+  {
+    float2 v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2* h2 = reinterpret_cast<const float2*>(hs + (c * TY + ty) * Q);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        v[c][s] = h2[j + s * T];
+        v[c][s + 4] = make_float2(0.f, 0.f);
+      }
+    }
+    fft_reg<Q, -1, true, 3>(v, j, lines, LS, lp.tw);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) lines[c * LS + pad16(j + r * T)] = v[c][r];
+  }
+  __syncthreads();
+  // split and store, TY rows of S contiguous:
+  // X_k = (Z_k + conj Z_{Q-k})/2 - (i/2) W^k (Z_k - conj Z_{Q-k}), X_Q = Re Z_0 - Im Z_0
+  for (int idx = tid; idx < nst; idx += NT) {
+    const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
+    const int yy = y0 + t;
+    if (yy >= ny) continue;
+    const float2* ln = sm + (3 * t + c) * LS;
+    const float2 zk = ln[pad16(k & (Q - 1))];
+    float2 xo;
+    if (k == Q) {
+      xo = make_float2(zk.x - zk.y, 0.f);
+    } else {
+      const float2 zq = ln[pad16((Q - k) & (Q - 1))];
+      const float2 a = cadd(zk, cconj(zq)), b = csub(zk, cconj(zq));
+      const float2 wb = cmul(__ldg(lp.tw + k * TWQ), b);
+      xo = make_float2(0.5f * (a.x + wb.y), 0.5f * (a.y - wb.x));
+    }
+    Sz[c * sc + (size_t)k * srow + yy] = xo;
+  }
+}
+
+template <int Q, int TY>
+cudaError_t launch_qt(int mode, const FilmDev* films, const LaunchP& lp, int nunits, size_t smem, cudaStream_t s) {
+  const unsigned threads = TY * (Q / 8);
+  switch (mode) {
+    case XM_R2C: return launch_pdl(kx_fast<Q, TY, XM_R2C>, nunits, threads, smem, s, films, lp);
+    case XM_HEFF: return launch_pdl(kx_fast<Q, TY, XM_HEFF>, nunits, threads, smem, s, films, lp);
+    case XM_ADJ1: return launch_pdl(kx_fast<Q, TY, XM_ADJ1>, nunits, threads, smem, s, films, lp);
+    case XM_ADJ2: return launch_pdl(kx_fast<Q, TY, XM_ADJ2>, nunits, threads, smem, s, films, lp);
+    case XM_HEUN1: return launch_pdl(kx_fast<Q, TY, XM_HEUN1>, nunits, threads, smem, s, films, lp);
+    case XM_HEUN2: return launch_pdl(kx_fast<Q, TY, XM_HEUN2>, nunits, threads, smem, s, films, lp);
+    default: return launch_pdl(kx_fast<Q, TY, XM_STEP>, nunits, threads, smem, s, films, lp);
+  }
+}
+
+template <int Q, int TY>
+cudaError_t attr_qt(size_t smem) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_R2C>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_HEFF>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_STEP>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_ADJ1>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_ADJ2>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_HEUN1>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_HEUN2>, a, (int)smem);
+  return e;
+}
+
+// Two tiles per length: the large one (x_tile(Q) lines) and one line per block, for
+// groups too small to fill the GPU with large tiles.
+template <int Q>
+cudaError_t launch_q(int mode, int TY, const FilmDev* films, const LaunchP& lp, int nunits, size_t smem,
+                     cudaStream_t s) {
+  if constexpr (x_tile(Q) > 1) {
+    if (TY == x_tile(Q)) return launch_qt<Q, x_tile(Q)>(mode, films, lp, nunits, smem, s);
+  }
+  if (TY == 1) return launch_qt<Q, 1>(mode, films, lp, nunits, smem, s);
+  return cudaErrorInvalidValue;
+}
+
+template <int Q>
+cudaError_t attr_q(int TY, size_t smem) {
+  if constexpr (x_tile(Q) > 1) {
+    if (TY == x_tile(Q)) return attr_qt<Q, x_tile(Q)>(smem);
+  }
+  if (TY == 1) return attr_qt<Q, 1>(smem);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fastx
+}  // namespace grace

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
   const int twq = Q > 0 ? GRACE_LMAX / (2 * Q) : 0;      // table step for W^k, P = 2Q
 
   const bool demag = (MODE == XM_STEP) || (MODE == XM_ADJ1) || (MODE == XM_ADJ2) ||
+                     (MODE == XM_HEUN1) || (MODE == XM_HEUN2) ||
                      (MODE == XM_HEFF && (lp.mask & 1u));
   if (demag) {
     for (int c = 0; c < 3; ++c) {
@@ -110,7 +111,8 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
       } else if constexpr (MODE == XM_ADJ2) {
         adj2_cell(f, lp, m, i, x, y, z, hdx, hdy, hdz);
       } else {
-        const unsigned mask = (MODE == XM_STEP) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
+        const unsigned mask =
+        (MODE == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
         const CellState cs = cell_field(f, mask, m, i, x, y, z, hdx, hdy, hdz);
         r = cell_apply<MODE>(f, lp, i, cs);
       }
@@ -454,6 +456,8 @@ cudaError_t configure_kernels(size_t smem_x, size_t smem_yz, size_t smem_y, size
   set((const void*)k_xpass<XM_STEP>, smem_x);
   set((const void*)k_xpass<XM_ADJ1>, smem_x);
   set((const void*)k_xpass<XM_ADJ2>, smem_x);
+  set((const void*)k_xpass<XM_HEUN1>, smem_x);
+  set((const void*)k_xpass<XM_HEUN2>, smem_x);
   set((const void*)k_yz, smem_yz);
   set((const void*)k_y<-1>, smem_y);
   set((const void*)k_y<+1>, smem_y);
@@ -469,6 +473,8 @@ cudaError_t launch_xpass(int mode, const FilmDev* films, const LaunchP& lp, int 
     case XM_HEFF: k_xpass<XM_HEFF><<<nunits, kThreads, smem, s>>>(films, lp); break;
     case XM_ADJ1: k_xpass<XM_ADJ1><<<nunits, kThreads, smem, s>>>(films, lp); break;
     case XM_ADJ2: k_xpass<XM_ADJ2><<<nunits, kThreads, smem, s>>>(films, lp); break;
+    case XM_HEUN1: k_xpass<XM_HEUN1><<<nunits, kThreads, smem, s>>>(films, lp); break;
+    case XM_HEUN2: k_xpass<XM_HEUN2><<<nunits, kThreads, smem, s>>>(films, lp); break;
     default: k_xpass<XM_STEP><<<nunits, kThreads, smem, s>>>(films, lp); break;
   }
   return cudaGetLastError();

@@ -54,8 +54,9 @@ struct FilmDev {
   const float* h_field;    // per-cell H_ext of this film or nullptr
 };
 
-// x-pass modes: R2C of Ms m; H_eff output; Euler step; the two halves of the adjoint.
-enum XMode { XM_R2C = 0, XM_HEFF = 1, XM_STEP = 2, XM_ADJ1 = 3, XM_ADJ2 = 4 };
+// x-pass modes: R2C of Ms m; H_eff output; Euler step; the two halves of the adjoint; the
+// two stages of a Heun step (stage 1 = the Euler predictor that also keeps k1 = f(m_n)).
+enum XMode { XM_R2C = 0, XM_HEFF = 1, XM_STEP = 2, XM_ADJ1 = 3, XM_ADJ2 = 4, XM_HEUN1 = 5, XM_HEUN2 = 6 };
 
 struct LaunchP {
   int nfilms;
@@ -68,6 +69,7 @@ struct LaunchP {
   int TQ;           // columns per block in the split z pass
   const float2* tw; // twiddle table, GRACE_LMAX entries
   int pdl;          // launch with programmatic stream serialization
+  float* k1;        // Heun: f(m_n), concatenated films (3 N)
   // adjoint (concatenated films; nullptr when unused)
   const float* mk;          // state to read instead of m[parity] (R2C, ADJ1, ADJ2)
   const float* adj_lam_in;  // lambda_{k+1}
