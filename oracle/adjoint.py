@@ -14,6 +14,7 @@ For a loss L(m_T), lambda_T = dL/dm_T and, per step from the last to the first,
   dL/dMs    += m.D(nu) - nu.(H_exch + H_anis)/Ms
 
 D is self-adjoint (N_ab = N_ba and N(-r) = N(r)), so D^T nu = D(nu) with unit weights.
+The applied field is constant in time here (no envelope).
 """
 from __future__ import annotations
 
@@ -58,6 +59,8 @@ def adjoint_step(m, lam_next, p: Params, dt: float, demag: Demag):
 
 def gradients(m0, p: Params, dt: float, steps: int, target, demag: Demag = None):
     """Loss and (dL/dm0, dL/dH_ext per cell, dL/dMs per cell) through ``steps`` Euler steps."""
+    if p.pulse is not None:
+        raise NotImplementedError("the adjoint takes a constant applied field")
     m = np.asarray(m0, dtype=np.float64)
     if demag is None:
         _, nz, ny, nx = m.shape

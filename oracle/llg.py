@@ -15,6 +15,11 @@ Euler), with these readings where the text is garbled or silent:
 * Energies (Eq. 1 times the cell volume V): E_exch = A V sum_bonds |m_j - m_i|^2/d^2,
   E_anis = Ku V sum (1 - m_x^2), E_demag = -(mu0/2) V sum Ms m.H_d,
   E_zeeman = -mu0 V sum Ms m.H_ext.
+* Time-dependent applied field (the input file's startTime / decayTime / stopTime,
+  Sec. 5, whose meaning the paper leaves open): H_ext(r, t) = s(t) H_ext(r) with s = 0
+  before t_start, 1 until t_decay, falling linearly to 0 at t_stop and 0 afterwards.
+  Euler evaluates the field at t_n; Heun's corrector at t_n + dt.  Time advances by
+  repeated addition t <- t + dt from t_0.
 """
 from __future__ import annotations
 
@@ -44,6 +49,22 @@ class Params:
     gamma0: float = 2.211e5
     hext: object = (0.0, 0.0, 0.0)
     r_switch: int = R_SWITCH
+    pulse: Optional[Sequence[float]] = None     # (t_start, t_decay, t_stop) in s, or constant
+
+
+def field_scale(t: float, pulse) -> float:
+    """Envelope s(t) of the applied field: 0 before t_start, 1 until t_decay, linear to 0
+    at t_stop, 0 after; 1 for a constant field (pulse None)."""
+    if pulse is None:
+        return 1.0
+    t0, t1, t2 = pulse
+    if t < t0:
+        return 0.0
+    if t < t1:
+        return 1.0
+    if t < t2:
+        return (t2 - t) / (t2 - t1)
+    return 0.0
 
 
 def laplacian(m, cell):
@@ -73,8 +94,8 @@ def anisotropy_field(m, p: Params):
     return h
 
 
-def zeeman_field(m, p: Params):
-    h = np.asarray(p.hext, dtype=np.float64)
+def zeeman_field(m, p: Params, t: float = 0.0):
+    h = field_scale(t, p.pulse) * np.asarray(p.hext, dtype=np.float64)
     if h.ndim == 1:
         return np.broadcast_to(h[:, None, None, None], np.shape(m)).copy()
     return h.copy()
@@ -94,8 +115,8 @@ class Demag:
         return demag_direct(m, Ms, self.cell, self.r_switch)
 
 
-def heff(m, p: Params, demag: Optional[Demag] = None, mask: int = ALL_TERMS):
-    """H_eff of Eq. 2 restricted to the terms in ``mask`` (A/m), layout [3][nz][ny][nx]."""
+def heff(m, p: Params, demag: Optional[Demag] = None, mask: int = ALL_TERMS, t: float = 0.0):
+    """H_eff of Eq. 2 at time t restricted to the terms in ``mask`` (A/m), layout [3][nz][ny][nx]."""
     m = np.asarray(m, dtype=np.float64)
     h = np.zeros_like(m)
     if mask & DEMAG:
@@ -108,7 +129,7 @@ def heff(m, p: Params, demag: Optional[Demag] = None, mask: int = ALL_TERMS):
     if mask & ANIS:
         h += anisotropy_field(m, p)
     if mask & ZEEMAN:
-        h += zeeman_field(m, p)
+        h += zeeman_field(m, p, t)
     return h
 
 
@@ -122,41 +143,45 @@ def normalise(v):
     return v / np.sqrt((v * v).sum(axis=0, keepdims=True))
 
 
-def euler_step(m, p: Params, dt: float, demag: Optional[Demag] = None):
-    """m_{n+1} = normalise(m_n + dt f(m_n, H_eff(m_n)))."""
+def euler_step(m, p: Params, dt: float, demag: Optional[Demag] = None, t: float = 0.0):
+    """m_{n+1} = normalise(m_n + dt f(m_n, H_eff(m_n, t_n)))."""
     m = np.asarray(m, dtype=np.float64)
-    return normalise(m + dt * llg_rhs(m, heff(m, p, demag), p.alpha, p.gamma0))
+    return normalise(m + dt * llg_rhs(m, heff(m, p, demag, t=t), p.alpha, p.gamma0))
 
 
-def heun_step(m, p: Params, dt: float, demag: Optional[Demag] = None):
+def heun_step(m, p: Params, dt: float, demag: Optional[Demag] = None, t: float = 0.0):
     """Explicit trapezoid (Heun) with renormalisation, the higher-order integrator the paper
-    names as future work (Sec. 6): k1 = f(m_n), m* = normalise(m_n + dt k1),
-    k2 = f(m*), m_{n+1} = normalise(m_n + dt (k1 + k2)/2)."""
+    names as future work (Sec. 6): k1 = f(m_n, t_n), m* = normalise(m_n + dt k1),
+    k2 = f(m*, t_n + dt), m_{n+1} = normalise(m_n + dt (k1 + k2)/2)."""
     m = np.asarray(m, dtype=np.float64)
-    k1 = llg_rhs(m, heff(m, p, demag), p.alpha, p.gamma0)
+    k1 = llg_rhs(m, heff(m, p, demag, t=t), p.alpha, p.gamma0)
     ms = normalise(m + dt * k1)
-    k2 = llg_rhs(ms, heff(ms, p, demag), p.alpha, p.gamma0)
+    k2 = llg_rhs(ms, heff(ms, p, demag, t=t + dt), p.alpha, p.gamma0)
     return normalise(m + 0.5 * dt * (k1 + k2))
 
 
 def run(m0, p: Params, dt: float, steps: int, demag: Optional[Demag] = None, keep=False,
-        integrator: str = "euler"):
-    """Take ``steps`` steps (Euler or Heun); returns the final state (and every state if ``keep``)."""
+        integrator: str = "euler", t0: float = 0.0):
+    """Take ``steps`` steps (Euler or Heun) from time t0; returns the final state (and every
+    state if ``keep``)."""
     m = np.asarray(m0, dtype=np.float64)
     if demag is None:
         _, nz, ny, nx = m.shape
         demag = Demag((nx, ny, nz), p.cell, "fft", p.r_switch)
     step = heun_step if integrator == "heun" else euler_step
     states = [m] if keep else None
+    t = float(t0)
     for _ in range(steps):
-        m = step(m, p, dt, demag)
+        m = step(m, p, dt, demag, t)
+        t = t + dt
         if keep:
             states.append(m)
     return (m, states) if keep else m
 
 
-def energies(m, p: Params, demag: Optional[Demag] = None):
-    """(E_exch, E_anis, E_demag, E_zeeman, E_total) in joules, from Eq. 1 times V per cell."""
+def energies(m, p: Params, demag: Optional[Demag] = None, t: float = 0.0):
+    """(E_exch, E_anis, E_demag, E_zeeman, E_total) in joules at time t, from Eq. 1 times V
+    per cell."""
     m = np.asarray(m, dtype=np.float64)
     dx, dy, dz = p.cell
     V = dx * dy * dz
@@ -169,7 +194,7 @@ def energies(m, p: Params, demag: Optional[Demag] = None):
     e_an = p.Ku * V * np.sum(1.0 - m[0] ** 2)
     hd = heff(m, p, demag, DEMAG)
     e_d = -0.5 * MU0 * V * np.sum(Ms * (m * hd).sum(axis=0))
-    hz = zeeman_field(m, p)
+    hz = zeeman_field(m, p, t)
     e_z = -MU0 * V * np.sum(Ms * (m * hz).sum(axis=0))
     return e_ex, e_an, e_d, e_z, e_ex + e_an + e_d + e_z
 

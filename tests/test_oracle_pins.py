@@ -273,12 +273,32 @@ def test_llg_torque_is_orthogonal_and_step_keeps_unit_length():
     assert np.abs(np.sqrt((m1 * m1).sum(0)) - 1).max() < 1e-14
 
 
-def _macrospin(dt, steps, alpha, H, theta0, phi0=0.0, integrator="euler"):
+def _macrospin(dt, steps, alpha, H, theta0, phi0=0.0, integrator="euler", pulse=None):
     cell = (2e-9, 2e-9, 2e-9)
     m0 = np.array([math.sin(theta0) * math.cos(phi0), math.sin(theta0) * math.sin(phi0),
                    math.cos(theta0)])[:, None, None, None]
-    p = llg.Params(cell, 8e5, 1.3e-11, 0.0, alpha, hext=(0.0, 0.0, H))
+    p = llg.Params(cell, 8e5, 1.3e-11, 0.0, alpha, hext=(0.0, 0.0, H), pulse=pulse)
     return llg.run(m0, p, dt, steps, llg.Demag((1, 1, 1), cell), integrator=integrator)[:, 0, 0, 0], p
+
+
+def _pulse_area(T, t0, t1, t2):
+    """Integral over [0, T] of the trapezoid envelope (0 | 1 from t0 | linear 1 -> 0 on [t1, t2])."""
+    if T <= t0:
+        return 0.0
+    if T <= t1:
+        return T - t0
+    if T <= t2:
+        r = T - t1
+        return (t1 - t0) + r - r * r / (2 * (t2 - t1))
+    return (t1 - t0) + 0.5 * (t2 - t1)
+
+
+def _macrospin_exact(H, alpha, th0, area, gamma0=2.211e5):
+    """Macrospin in H(t) z: phi = g/(1+a^2) int H, tan(theta/2) decays by exp(-a g/(1+a^2) int H)."""
+    c = gamma0 * H / (1 + alpha ** 2)
+    th = 2 * math.atan(math.tan(th0 / 2) * math.exp(-alpha * c * area))
+    ph = c * area
+    return np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
 
 
 def test_macrospin_closed_form_first_order():
@@ -312,6 +332,62 @@ def test_heun_macrospin_second_order():
         errs.append(np.abs(m - ref).max())
     assert errs[1] < 5e-4
     assert 3.3 < errs[0] / errs[1] < 4.7, errs
+
+
+@pytest.mark.parametrize("T", [1.6e-11, 2.4e-11])        # inside the ramp, after the stop
+def test_pulsed_field_macrospin_euler(T):
+    """Trapezoid field pulse (off until 2 ps, full until 8 ps, linear to zero at 20 ps) on the
+    macrospin: the exact solution depends on the pulse only through its area up to T.  Euler
+    samples the field at the start of each step, so with the edges on step boundaries its
+    error is first order (ratio ~2 per halving) and small."""
+    H, alpha, th0, pulse = 1.2e5, 0.2, 1.2, (2e-12, 8e-12, 2e-11)
+    ref = _macrospin_exact(H, alpha, th0, _pulse_area(T, *pulse))
+    errs = []
+    for dt in (2e-13, 1e-13):
+        m, _ = _macrospin(dt, int(round(T / dt)), alpha, H, th0, pulse=pulse)
+        errs.append(np.abs(m - ref).max())
+    assert errs[1] < 2e-2
+    assert 1.7 < errs[0] / errs[1] < 2.3, errs
+
+
+@pytest.mark.parametrize("T", [1.6e-11, 2.4e-11])
+def test_pulsed_field_macrospin_heun_second_order(T):
+    """Heun on a pulse that is on from t = 0 and ramps down linearly from 8 ps to 20 ps:
+    the envelope is continuous with kinks on step boundaries, so the trapezoid rule in
+    time keeps second order (ratio ~4 per halving).  A corrector that sampled the field at
+    t_n instead of t_n + dt would fall to first order inside the ramp."""
+    H, alpha, th0, pulse = 1.2e5, 0.2, 1.2, (0.0, 8e-12, 2e-11)
+    ref = _macrospin_exact(H, alpha, th0, _pulse_area(T, *pulse))
+    errs = []
+    for dt in (4e-13, 2e-13):
+        m, _ = _macrospin(dt, int(round(T / dt)), alpha, H, th0, integrator="heun", pulse=pulse)
+        errs.append(np.abs(m - ref).max())
+    assert errs[1] < 5e-4
+    assert 3.3 < errs[0] / errs[1] < 4.7, errs
+
+
+def test_euler_samples_field_at_step_start():
+    """Explicit Euler takes f(t_n, m_n): with the pulse switching on exactly at t = dt the
+    first step sees no field (m unchanged), and the second step is one Euler step of the
+    constant-field macrospin."""
+    dt, H, alpha, th0 = 1e-13, 1e5, 0.1, 0.9
+    pulse = (dt, 1.0, 1.0)
+    m1, _ = _macrospin(dt, 1, alpha, H, th0, pulse=pulse)
+    m0 = np.array([math.sin(th0), 0.0, math.cos(th0)])
+    assert np.abs(m1 - m0).max() < 1e-14
+    m2, _ = _macrospin(dt, 2, alpha, H, th0, pulse=pulse)
+    c = 2.211e5 / (1 + alpha ** 2)
+    h = np.array([0.0, 0.0, H])
+    u = m0 - dt * c * (np.cross(m0, h) + alpha * np.cross(m0, np.cross(m0, h)))
+    assert np.abs(m2 - u / np.linalg.norm(u)).max() < 1e-12
+
+
+def test_pulse_off_leaves_macrospin_still():
+    """Before t_start the applied field is zero and a cube's own demag field is parallel to
+    m, so nothing moves."""
+    m, _ = _macrospin(1e-13, 50, 0.1, 1e5, 0.9, phi0=0.4, pulse=(1e-11, 2e-11, 3e-11))
+    ref = np.array([math.sin(0.9) * math.cos(0.4), math.sin(0.9) * math.sin(0.4), math.cos(0.9)])
+    assert np.abs(m - ref).max() < 1e-14
 
 
 def test_kittel_frequency_of_flat_cell():
