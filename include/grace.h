@@ -145,6 +145,25 @@ int grace_set_hext_field(grace_ctx *ctx, const float *dev_h);
 int grace_set_ms_field(grace_ctx *ctx, const float *dev_ms);
 
 /*
+ * grace_set_hext_pulse - time envelope of the applied field, after the input file's
+ * startTime / decayTime / stopTime (Sec. 5; the paper does not define them, this is the
+ * reading used): H_ext(r, t) = s(t) (uniform H_ext + per-cell field), with
+ *   s = 0 for t < t_start, 1 for t_start <= t < t_decay,
+ *   (t_stop - t)/(t_stop - t_decay) for t_decay <= t < t_stop, 0 for t >= t_stop.
+ * times_s = {t_start, t_decay, t_stop} in seconds (finite, non-decreasing), or NULL for a
+ * constant field (s = 1, the default).  Explicit Euler takes s(t_n), Heun's corrector
+ * s(t_n + dt); grace_heff and grace_energy use s at the current time.  While an envelope
+ * is set, every step launches one extra single-thread kernel that computes s and
+ * advances the device copy of t; grace_backward returns GRACE_EUNSUPPORTED.
+ */
+int grace_set_hext_pulse(grace_ctx *ctx, const double times_s[3]);
+
+/* Time of the current state in seconds (default 0; finite).  grace_step adds dt_s once per
+ * step, in FP64, on the host and on the device alike; grace_set_m leaves it unchanged. */
+int grace_set_time(grace_ctx *ctx, double t_s);
+int grace_get_time(const grace_ctx *ctx, double *t_s);
+
+/*
  * grace_heff - H_eff of the current state restricted to term_mask (Eq. 2), written to
  * dev_h (3*N floats).  The state is unchanged.
  */

@@ -36,6 +36,9 @@ SIGNATURES = {
     "grace_set_film_hext": (_I, [_P, _I, _DP]),
     "grace_set_hext_field": (_I, [_P, _P]),
     "grace_set_ms_field": (_I, [_P, _P]),
+    "grace_set_hext_pulse": (_I, [_P, _DP]),
+    "grace_set_time": (_I, [_P, _D]),
+    "grace_get_time": (_I, [_P, _DP]),
     "grace_heff": (_I, [_P, _P, C.c_uint]),
     "grace_step": (_I, [_P, _I, _D]),
     "grace_energy": (_I, [_P, _DP, _DP]),

@@ -77,6 +77,7 @@ struct grace_ctx {
   long long ncell = 0;
   int tile_x = 0, tile_yz = 0;      // 0 = automatic
   size_t o_tw = 0, o_films = 0, o_run = 0, o_m0 = 0, o_m1 = 0, o_H = 0, o_k1 = 0, o_part = 0, o_eout = 0;
+  size_t o_time = 0;                // device time (double) and envelope scale {s(t), s(t + dt)}
   std::vector<size_t> o_S;
   size_t run_bytes = 0, build_bytes = 0, need = 0;
   char* ws = nullptr;
@@ -89,10 +90,13 @@ struct grace_ctx {
   bool use_graph = true;
   bool pdl = true;
   int integrator = 0;               // 0: explicit Euler, 1: Heun
+  double t = 0.0;                   // time of the current state (s)
+  bool pulse = false;               // applied field scaled by a trapezoid envelope
+  double pulse_t[3] = {0.0, 0.0, 0.0};
   int graph_steps = 16;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  float gdt[2] = {0.f, 0.f};
+  double gdt[2] = {0.0, 0.0};
   bool trace = false;
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kind;
@@ -397,6 +401,8 @@ int plan(grace_ctx* c) {
   r = al256(r + (size_t)kEnergyBlocks * 8 * sizeof(double));
   c->o_eout = r;
   r = al256(r + 8 * sizeof(double));
+  c->o_time = r;
+  r = al256(r + 2 * sizeof(double));
   c->run_bytes = r;
   size_t b = 0;
   for (auto& s : c->classes) {
@@ -439,6 +445,11 @@ int upload_films(grace_ctx* c) {
   return GRACE_OK;
 }
 
+double* dev_time(const grace_ctx* c) { return reinterpret_cast<double*>(c->ws + c->o_run + c->o_time); }
+float* time_scale(const grace_ctx* c) {
+  return reinterpret_cast<float*>(c->ws + c->o_run + c->o_time + sizeof(double));
+}
+
 LaunchP group_lp(const grace_ctx* c, const Group& g) {
   LaunchP lp{};
   lp.nfilms = (int)g.idx.size();
@@ -452,6 +463,7 @@ LaunchP group_lp(const grace_ctx* c, const Group& g) {
   lp.tw = reinterpret_cast<const float2*>(c->ws + c->o_tw);
   lp.pdl = c->pdl ? 1 : 0;
   lp.k1 = reinterpret_cast<float*>(c->ws + c->o_run + c->o_k1);
+  lp.hscale = c->pulse ? time_scale(c) : nullptr;
   return lp;
 }
 
@@ -516,7 +528,11 @@ cudaError_t enqueue_x(grace_ctx* c, const Group& g, int mode, const LaunchP& lp,
 // One time step from the state in buffer `parity`.  Euler leaves the new state in the other
 // buffer; Heun (predictor into the other buffer, corrector back into this one) leaves it in
 // the same buffer.
-cudaError_t enqueue_step(grace_ctx* c, int parity, float dt, cudaStream_t s) {
+cudaError_t enqueue_step(grace_ctx* c, int parity, float dt, double ddt, cudaStream_t s) {
+  if (c->pulse) {   // envelope at t_n and t_n + dt for this step, then t <- t + dt
+    cudaError_t e = launch_field_time(dev_time(c), time_scale(c), ddt, true, c->pulse_t, s);
+    if (e != cudaSuccess) return e;
+  }
   for (const auto& g : c->groups) {
     LaunchP lp = group_lp(c, g);
     lp.parity = parity;
@@ -551,6 +567,10 @@ cudaError_t enqueue_r2c(grace_ctx* c) {
 }
 
 int enqueue_heff(grace_ctx* c, float* out, unsigned mask) {
+  if (c->pulse) {   // envelope at the current time, no advance
+    cudaError_t e = launch_field_time(dev_time(c), time_scale(c), 0.0, false, c->pulse_t, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "field envelope launch");
+  }
   for (const auto& g : c->groups) {
     LaunchP lp = group_lp(c, g);
     lp.mask = mask;
@@ -731,6 +751,8 @@ int grace_bind(grace_ctx* c, void* dev_ws, size_t bytes, void* cuda_stream) {
   int st = upload_films(c);
   if (st != GRACE_OK) return st;
   GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
+  GRACE_CUDA(c, launch_set_time(dev_time(c), c->t, c->stream));
+  GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
   if (c->use_graph && !c->cap) GRACE_CUDA(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   c->bound = true;
   return GRACE_OK;
@@ -827,6 +849,36 @@ int grace_set_ms_field(grace_ctx* c, const float* dev_ms) {
   return GRACE_OK;
 }
 
+int grace_set_hext_pulse(grace_ctx* c, const double times[3]) {
+  if (!c) return GRACE_EINVAL;
+  if (times) {
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(times[k])) return fail(c, GRACE_EINVAL, "pulse times must be finite");
+    if (!(times[0] <= times[1] && times[1] <= times[2]))
+      return fail(c, GRACE_EINVAL, "pulse times must satisfy t_start <= t_decay <= t_stop");
+    for (int k = 0; k < 3; ++k) c->pulse_t[k] = times[k];
+  }
+  c->pulse = times != nullptr;
+  drop_graphs(c);   // the envelope kernel and its times are part of a captured step
+  // the device time only advances while an envelope is set: bring it to the host's
+  if (c->pulse && c->ws) GRACE_CUDA(c, launch_set_time(dev_time(c), c->t, c->stream));
+  return GRACE_OK;
+}
+
+int grace_set_time(grace_ctx* c, double t) {
+  if (!c) return GRACE_EINVAL;
+  if (!std::isfinite(t)) return fail(c, GRACE_EINVAL, "time must be finite");
+  c->t = t;
+  if (c->ws) GRACE_CUDA(c, launch_set_time(dev_time(c), t, c->stream));
+  return GRACE_OK;
+}
+
+int grace_get_time(const grace_ctx* c, double* t) {
+  if (!c || !t) return GRACE_EINVAL;
+  *t = c->t;
+  return GRACE_OK;
+}
+
 int grace_heff(grace_ctx* c, float* dev_h, unsigned mask) {
   int st = ready(c, true);
   if (st) return st;
@@ -843,9 +895,10 @@ int grace_step(grace_ctx* c, int n, double dt) {
   const float fdt = (float)dt;
   int done = 0;
   const int G = c->graph_steps;
+  for (int k = 0; k < n; ++k) c->t += dt;   // host copy of the time, summed as the device sums it
   if (c->use_graph && c->cap && !c->trace && n >= G) {
     const int p = c->parity;
-    if (!c->gexec[p] || c->gdt[p] != fdt) {
+    if (!c->gexec[p] || c->gdt[p] != dt) {
       if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
       c->gexec[p] = nullptr;
       cudaGraph_t g = nullptr;
@@ -855,7 +908,7 @@ int grace_step(grace_ctx* c, int n, double dt) {
       const bool pdl = c->pdl;
       c->pdl = false;
       for (int s = 0; s < G && e == cudaSuccess; ++s)
-        e = enqueue_step(c, (p + s * parity_flip(c)) & 1, fdt, c->cap);
+        e = enqueue_step(c, (p + s * parity_flip(c)) & 1, fdt, dt, c->cap);
       c->pdl = pdl;
       cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
       if (e != cudaSuccess) {
@@ -866,7 +919,7 @@ int grace_step(grace_ctx* c, int n, double dt) {
       e = cudaGraphInstantiate(&c->gexec[p], g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
-      c->gdt[p] = fdt;
+      c->gdt[p] = dt;
     }
     while (n - done >= G) {
       GRACE_CUDA(c, cudaGraphLaunch(c->gexec[p], c->stream));
@@ -874,7 +927,7 @@ int grace_step(grace_ctx* c, int n, double dt) {
     }
   }
   for (; done < n; ++done) {
-    GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, c->stream));
+    GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, dt, c->stream));
     c->parity ^= parity_flip(c);
   }
   return GRACE_OK;
@@ -889,6 +942,7 @@ int grace_energy(grace_ctx* c, double out[5], double mavg[3]) {
   LaunchP lp{};
   lp.nfilms = (int)c->films.size();
   lp.parity = c->parity;
+  lp.hscale = c->pulse ? time_scale(c) : nullptr;   // enqueue_heff left s(t) in it
   double* part = reinterpret_cast<double*>(c->ws + c->o_run + c->o_part);
   double* res = reinterpret_cast<double*>(c->ws + c->o_run + c->o_eout);
   GRACE_CUDA(c, launch_energy(dfilms(c), lp, H, c->ncell, part, kEnergyBlocks, res, c->stream));
@@ -941,6 +995,7 @@ int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt
   if (st) return st;
   if (!dL_dmT) return fail(c, GRACE_EINVAL, "dL/dm_T pointer is NULL");
   if (c->integrator != 0) return fail(c, GRACE_EUNSUPPORTED, "the adjoint is built for the Euler integrator");
+  if (c->pulse) return fail(c, GRACE_EUNSUPPORTED, "the adjoint takes a constant applied field");
   if (n < 0 || ckpt < 1) return fail(c, GRACE_EINVAL, "n must be >= 0 and ckpt_every >= 1");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GRACE_EINVAL, "dt must be positive");
   size_t need = 0;
@@ -967,7 +1022,7 @@ int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt
   if ((st = copy_state(c, ck0, cur_m(c)))) return st;
   for (int s = 1; s < nck; ++s) {
     for (int k = 0; k < ckpt; ++k) {
-      GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, c->stream));
+      GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, dt, c->stream));
       c->parity ^= 1;
     }
     if ((st = copy_state(c, state(s), cur_m(c)))) return st;
@@ -982,7 +1037,7 @@ int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt
     for (int j = 0; j < len; ++j) {
       if ((st = copy_state(c, seg0 + (size_t)j * (sb / sizeof(float)), cur_m(c)))) return st;
       if (j + 1 < len) {
-        GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, c->stream));
+        GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, dt, c->stream));
         c->parity ^= 1;
       }
     }

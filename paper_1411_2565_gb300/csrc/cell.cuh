@@ -47,8 +47,10 @@ __device__ __forceinline__ float3 laplacian(const FilmDev& f, const float* __res
 
 // m at cell i and its H_eff restricted to `mask` with hd as the demag part.  All global
 // loads of a cell happen here, so callers batch several cells' calls before using them.
+// hs scales the applied field (its time envelope; 1 for a constant field).
 __device__ __forceinline__ CellState cell_field(const FilmDev& f, unsigned mask, const float* __restrict__ m,
-                                                int i, int x, int y, int z, float hdx, float hdy, float hdz) {
+                                                int i, int x, int y, int z, float hdx, float hdy, float hdz,
+                                                float hs = 1.f) {
   const int N = f.ncell;
   CellState c;
   c.mx = m[i];
@@ -66,14 +68,15 @@ __device__ __forceinline__ CellState cell_field(const FilmDev& f, unsigned mask,
   }
   if (mask & 4u) hx = fmaf(f.ms_field ? f.can * rms : f.can_ms, c.mx, hx);
   if (mask & 8u) {
-    hx += f.hx;
-    hy += f.hy;
-    hz += f.hz;
+    float ex = f.hx, ey = f.hy, ez = f.hz;
     if (f.h_field) {
-      hx += f.h_field[i];
-      hy += f.h_field[N + i];
-      hz += f.h_field[2 * N + i];
+      ex += f.h_field[i];
+      ey += f.h_field[N + i];
+      ez += f.h_field[2 * N + i];
     }
+    hx = fmaf(hs, ex, hx);
+    hy = fmaf(hs, ey, hy);
+    hz = fmaf(hs, ez, hz);
   }
   c.hx = hx;
   c.hy = hy;

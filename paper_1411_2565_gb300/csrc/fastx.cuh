@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
   // each thread owns 8 cells and issues the loads of 4 of them before using any
     const unsigned mask =
         (MODE == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
+    const float hsc = lp.hscale ? lp.hscale[MODE == XM_HEUN2 ? 1 : 0] : 1.f;
     constexpr int U = 4;
     for (int base = 0; base < TY * Q; base += U * NT) {
       CellState cs[U];
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
         ok[u] = idx < TY * Q && x < nx && y < ny;
         if (ok[u]) {
           const float* hp = hs + t * Q + x;
-          cs[u] = cell_field(f, mask, m, (z * ny + y) * nx + x, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q]);
+          cs[u] = cell_field(f, mask, m, (z * ny + y) * nx + x, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q], hsc);
         }
       }
 #pragma unroll

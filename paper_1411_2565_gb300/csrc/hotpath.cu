@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
       } else {
         const unsigned mask =
         (MODE == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
-        const CellState cs = cell_field(f, mask, m, i, x, y, z, hdx, hdy, hdz);
+        const float hsc = lp.hscale ? lp.hscale[MODE == XM_HEUN2 ? 1 : 0] : 1.f;
+        const CellState cs = cell_field(f, mask, m, i, x, y, z, hdx, hdy, hdz, hsc);
         r = cell_apply<MODE>(f, lp, i, cs);
       }
     }
@@ -417,7 +418,8 @@ __global__ void __launch_bounds__(kEThreads) k_energy(const FilmDev* __restrict_
       hy += f.h_field[N + i];
       hz += f.h_field[2 * N + i];
     }
-    acc[3] += -kMu0 * f.V * Ms * (mx * hx + my * hy + mz * hz);
+    const double hsc = lp.hscale ? (double)lp.hscale[0] : 1.0;
+    acc[3] += -kMu0 * f.V * Ms * hsc * (mx * hx + my * hy + mz * hz);
     acc[4] += mx;
     acc[5] += my;
     acc[6] += mz;
@@ -432,6 +434,28 @@ __global__ void __launch_bounds__(kEThreads) k_energy(const FilmDev* __restrict_
     __syncthreads();
   }
   if (threadIdx.x < 8) partial[(size_t)blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Trapezoid envelope of the applied field: 0 before t_start, 1 until t_decay, linear to
+// 0 at t_stop, 0 afterwards (FP64, the same comparisons as the host-side definition).
+__device__ double field_envelope(double t, double t0, double t1, double t2) {
+  if (t < t0) return 0.0;
+  if (t < t1) return 1.0;
+  if (t < t2) return (t2 - t) / (t2 - t1);
+  return 0.0;
+}
+
+__global__ void k_field_time(double* __restrict__ t, float* __restrict__ scale, double dt, int advance,
+                             double t0, double t1, double t2) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double tn = *t;
+  scale[0] = (float)field_envelope(tn, t0, t1, t2);
+  scale[1] = (float)field_envelope(tn + dt, t0, t1, t2);
+  if (advance) *t = tn + dt;
+}
+
+__global__ void k_set_time(double* __restrict__ t, double value) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *t = value;
 }
 
 // Fixed-order sum of the block partials (deterministic).
@@ -497,6 +521,17 @@ cudaError_t launch_y(int dir, const FilmDev* films, const LaunchP& lp, int nunit
 cudaError_t launch_z(const FilmDev* films, const LaunchP& lp, int nunits, size_t smem, cudaStream_t s) {
   if (nunits <= 0) return cudaSuccess;
   k_z<<<nunits, kThreads, smem, s>>>(films, lp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_time(double* t, float* scale, double dt, bool advance, const double pulse[3],
+                              cudaStream_t s) {
+  k_field_time<<<1, 32, 0, s>>>(t, scale, dt, advance ? 1 : 0, pulse[0], pulse[1], pulse[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_time(double* t, double value, cudaStream_t s) {
+  k_set_time<<<1, 32, 0, s>>>(t, value);
   return cudaGetLastError();
 }
 

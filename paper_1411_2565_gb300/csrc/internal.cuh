@@ -70,6 +70,7 @@ struct LaunchP {
   const float2* tw; // twiddle table, GRACE_LMAX entries
   int pdl;          // launch with programmatic stream serialization
   float* k1;        // Heun: f(m_n), concatenated films (3 N)
+  const float* hscale;  // applied-field envelope {s(t_n), s(t_n + dt)}, nullptr: constant field
   // adjoint (concatenated films; nullptr when unused)
   const float* mk;          // state to read instead of m[parity] (R2C, ADJ1, ADJ2)
   const float* adj_lam_in;  // lambda_{k+1}
@@ -124,6 +125,11 @@ cudaError_t launch_yz(const FilmDev* films, const LaunchP& lp, int nunits, size_
 cudaError_t launch_y(int dir, const FilmDev* films, const LaunchP& lp, int nunits, size_t smem,
                      cudaStream_t s);
 cudaError_t launch_z(const FilmDev* films, const LaunchP& lp, int nunits, size_t smem, cudaStream_t s);
+// Applied-field envelope: scale = {s(t), s(t + dt)} from the device time *t, which
+// then advances by dt when `advance`; and a plain store of the device time.
+cudaError_t launch_field_time(double* t, float* scale, double dt, bool advance, const double pulse[3],
+                              cudaStream_t s);
+cudaError_t launch_set_time(double* t, double value, cudaStream_t s);
 cudaError_t launch_energy(const FilmDev* films, const LaunchP& lp, const float* hdemag,
                           long long ntotal, double* partial, int nblocks, double* result,
                           cudaStream_t s);

@@ -89,6 +89,22 @@ class _Base:
         check(self._L.grace_set_ms_field(self.ctx, ptr), "grace_set_ms_field", self.ctx)
         self._keep["ms"] = ms
 
+    def set_hext_pulse(self, times: Optional[Sequence[float]]):
+        """Applied-field envelope (t_start, t_decay, t_stop) in s, or None for a constant field
+        (grace_set_hext_pulse)."""
+        arg = None if times is None else dvec(times)
+        check(self._L.grace_set_hext_pulse(self.ctx, arg), "grace_set_hext_pulse", self.ctx)
+
+    @property
+    def time(self) -> float:
+        t = C.c_double()
+        check(self._L.grace_get_time(self.ctx, C.byref(t)), "grace_get_time", self.ctx)
+        return t.value
+
+    @time.setter
+    def time(self, t: float):
+        check(self._L.grace_set_time(self.ctx, float(t)), "grace_set_time", self.ctx)
+
     def trace(self, capacity: int = 1 << 16):
         """Time the next ``capacity`` kernel launches with CUDA events (0 switches it off)."""
         check(self._L.grace_trace(self.ctx, int(capacity)), "grace_trace", self.ctx)

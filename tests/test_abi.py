@@ -104,3 +104,22 @@ def test_batch_create_shares_tensor_per_shape(lib):
     lib.grace_destroy(ctx)
     bad = C.c_void_p()
     assert lib.grace_batch_create(C.byref(bad), 0, None, None, None, None, None, None, None) == EINVAL
+
+
+def test_pulse_and_time_validation(lib):
+    """Envelope times must be finite and non-decreasing; the time is kept on the host before
+    grace_bind (no device call)."""
+    st, ctx = _create(lib)
+    assert st == 0
+    for bad in ([1e-9, 0.5e-9, 2e-9], [0.0, 1e-9, 0.5e-9], [0.0, float("nan"), 1e-9],
+                [0.0, 1e-9, float("inf")]):
+        assert lib.grace_set_hext_pulse(ctx, _lib.dvec(bad)) == EINVAL
+    assert lib.grace_set_hext_pulse(ctx, _lib.dvec([0.0, 1e-9, 1e-9])) == 0
+    assert lib.grace_set_hext_pulse(ctx, None) == 0
+    t = C.c_double()
+    assert lib.grace_get_time(ctx, C.byref(t)) == 0 and t.value == 0.0
+    assert lib.grace_set_time(ctx, 2.5e-10) == 0
+    assert lib.grace_get_time(ctx, C.byref(t)) == 0 and t.value == 2.5e-10
+    assert lib.grace_set_time(ctx, float("inf")) == EINVAL
+    assert lib.grace_get_time(ctx, None) == EINVAL
+    assert lib.grace_destroy(ctx) == 0
