@@ -84,6 +84,16 @@ def s_state_m(shape_zyx: Tuple[int, int, int], seed: int, noise: float = 0.01) -
     return np.ascontiguousarray(m.astype(np.float32))
 
 
+def near_saturated_m(shape_zyx: Tuple[int, int, int], direction, seed: int, noise: float = 0.02) -> np.ndarray:
+    """Uniform m along `direction` plus uniform +-noise per component, normalised; FP32
+    [3][nz][ny][nx] (the near-saturated start of the standard-problem-4 relaxation)."""
+    d = np.asarray(direction, dtype=np.float64)
+    m = np.broadcast_to((d / np.linalg.norm(d))[:, None, None, None], (3,) + tuple(shape_zyx)).copy()
+    m += noise * (2.0 * uniform(seed, m.size).reshape(m.shape) - 1.0)
+    m /= np.sqrt((m * m).sum(axis=0, keepdims=True))
+    return np.ascontiguousarray(m.astype(np.float32))
+
+
 def smooth_target(shape_zyx: Tuple[int, int, int], seed: int) -> np.ndarray:
     """Smooth unit target field normalise(cos(2 pi x/Lx + p1), sin(2 pi y/Ly + p2), 0.3 cos(2 pi (x+y)/Lx + p3))."""
     nz, ny, nx = shape_zyx
