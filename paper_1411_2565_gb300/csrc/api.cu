@@ -369,7 +369,7 @@ int plan(grace_ctx* c) {
   // workspace layout: [twiddles | descriptors | tensors | runtime (aliased by build scratch)]
   size_t o = 0;
   c->o_tw = o;
-  o = al256(o + (size_t)GRACE_LMAX * sizeof(float2));
+  o = al256(o + (size_t)(2 * GRACE_LMAX - 2) * sizeof(float2));
   c->o_films = o;
   o = al256(o + c->films.size() * sizeof(FilmDev));
   for (auto& g : c->groups) {
@@ -460,7 +460,8 @@ LaunchP group_lp(const grace_ctx* c, const Group& g) {
   lp.TY = g.TY;
   lp.RPB = g.RPB;
   lp.TQ = g.TQ;
-  lp.tw = reinterpret_cast<const float2*>(c->ws + c->o_tw);
+  lp.twb = reinterpret_cast<const float2*>(c->ws + c->o_tw);
+  lp.tw = lp.twb + (GRACE_LMAX - 2);   // the base-GRACE_LMAX table
   lp.pdl = c->pdl ? 1 : 0;
   lp.k1 = reinterpret_cast<float*>(c->ws + c->o_run + c->o_k1);
   lp.hscale = c->pulse ? time_scale(c) : nullptr;
@@ -693,12 +694,14 @@ int grace_bind(grace_ctx* c, void* dev_ws, size_t bytes, void* cuda_stream) {
   c->mset = false;
   c->parity = 0;
   GRACE_CUDA(c, configure_all(c));
-  // twiddle table exp(-2 pi i m / LMAX), FP64 on the host, rounded to FP32
-  std::vector<float2> tw(GRACE_LMAX);
-  for (int m = 0; m < GRACE_LMAX; ++m) {
-    const double a = 2.0 * M_PI * (double)m / GRACE_LMAX;
-    tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
-  }
+  // twiddle tables exp(-2 pi i k / B) for B = 2, 4, ..., LMAX, end to end (table B at
+  // offset B - 2), FP64 on the host, rounded to FP32
+  std::vector<float2> tw(2 * GRACE_LMAX - 2);
+  for (int B = 2; B <= GRACE_LMAX; B *= 2)
+    for (int k = 0; k < B; ++k) {
+      const double a = 2.0 * M_PI * (double)k / (double)B;
+      tw[B - 2 + k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
   GRACE_CUDA(c, cudaMemcpyAsync(c->ws + c->o_tw, tw.data(), tw.size() * sizeof(float2),
                                 cudaMemcpyHostToDevice, c->stream));
   // demag tensors, one per shape class, built in the (aliased) runtime region

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) ky_fast(const FilmDev* __restrict__ films
       v[0][r] = (ok && y < ny) ? S[y] : make_float2(0.f, 0.f);
       v[0][r + 4] = make_float2(0.f, 0.f);
     }
-    fft_reg<PY, -1, true, 1>(v, j, line, LS, lp.tw);
+    fft_reg<PY, -1, true, 1>(v, j, line, LS, lp.twb);
     if (ok) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) S[j + r * T] = v[0][r];
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) ky_fast(const FilmDev* __restrict__ films
   } else {
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[0][r] = ok ? S[j + r * T] : make_float2(0.f, 0.f);
-    fft_reg<PY, +1, false, 1>(v, j, line, LS, lp.tw);
+    fft_reg<PY, +1, false, 1>(v, j, line, LS, lp.twb);
     if (ok) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256, 2) kz_fast(const FilmDev* __restrict__ fi
       v[c][r + 4] = make_float2(0.f, 0.f);
     }
   }
-  fft_reg<PZ, -1, true, 3>(v, j, lines, gs, lp.tw);
+  fft_reg<PZ, -1, true, 3>(v, j, lines, gs, lp.twb);
   if (ok) {
     const int kx = q / Py, ky = q - kx * Py;
     const bool ylo = ky <= Py / 2;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256, 2) kz_fast(const FilmDev* __restrict__ fi
       v[2][r] = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
     }
   }
-  fft_reg<PZ, +1, false, 3>(v, j, lines, gs, lp.tw);
+  fft_reg<PZ, +1, false, 3>(v, j, lines, gs, lp.twb);
   if (ok) {
 #pragma unroll
     for (int c = 0; c < 3; ++c)

@@ -36,7 +36,6 @@ __host__ __device__ constexpr int x_tile(int Q) {
 template <int Q, int TY, int MODE>
 __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = Q / 8;
-  constexpr int TWQ = GRACE_LMAX / (2 * Q);
   constexpr int NT = TY * T;
   constexpr int LS = x_line_stride(Q, TY);
   const int tid = threadIdx.x;
@@ -99,7 +98,7 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
     for (int r = 0; r < 8; ++r) {
       // C_k = (X_k + conj X_{Q-k}) + i W^{-k} (X_k - conj X_{Q-k})
       const int k = j + r * T;
-      const float2 w = cconj(__ldg(lp.tw + k * TWQ));
+      const float2 w = twb_at<+1>(lp.twb, 2 * Q, k);   // W^{-k}, P = 2Q
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float2 xk = lines[c * LS + pad16(k)], xq = lines[c * LS + pad16(Q - k)];
@@ -109,7 +108,7 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
       }
     }
     __syncthreads();
-    fft_reg<Q, +1, false, 3>(v, j, lines, LS, lp.tw);
+    fft_reg<Q, +1, false, 3>(v, j, lines, LS, lp.twb);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       float2* h2 = reinterpret_cast<float2*>(hs + (c * TY + ty) * Q);
@@ -184,7 +183,7 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
         v[c][s + 4] = make_float2(0.f, 0.f);
       }
     }
-    fft_reg<Q, -1, true, 3>(v, j, lines, LS, lp.tw);
+    fft_reg<Q, -1, true, 3>(v, j, lines, LS, lp.twb);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -205,7 +204,7 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
     } else {
       const float2 zq = ln[pad16((Q - k) & (Q - 1))];
       const float2 a = cadd(zk, cconj(zq)), b = csub(zk, cconj(zq));
-      const float2 wb = cmul(__ldg(lp.tw + k * TWQ), b);
+      const float2 wb = cmul(twb_at<-1>(lp.twb, 2 * Q, k), b);
       xo = make_float2(0.5f * (a.x + wb.y), 0.5f * (a.y - wb.x));
     }
     Sz[c * sc + (size_t)k * srow + yy] = xo;

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256, 3) kyz_fast(const FilmDev* __restrict__ f
       v[c][r + 4] = make_float2(0.f, 0.f);
     }
   }
-  fft_reg<PY, -1, true, 3>(v, j, lines, NZ * LS, lp.tw);
+  fft_reg<PY, -1, true, 3>(v, j, lines, NZ * LS, lp.twb);
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256, 3) kyz_fast(const FilmDev* __restrict__ f
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[c][r] = lines[c * NZ * LS + pad16(j + r * T)];
   __syncthreads();
-  fft_reg<PY, +1, false, 3>(v, j, lines, NZ * LS, lp.tw);
+  fft_reg<PY, +1, false, 3>(v, j, lines, NZ * LS, lp.twb);
   if (!ok) return;
   float2* S1 = f.S + ((size_t)z * f.Kx + kx) * f.srow;
 #pragma unroll

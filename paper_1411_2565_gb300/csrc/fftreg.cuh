@@ -32,6 +32,14 @@ __host__ __device__ constexpr int fast_line_stride(int L, int shift) {
   return ((L + L / 8 + 1 + 15) / 16) * 16 + (shift & 15);
 }
 
+// Per-base twiddle tables (one contiguous table per power-of-two base B, laid end to end:
+// exp(-2 pi i k / B) at twb[B - 2 + k]): a stage reads w^k, w^2k, w^4k from the tables of
+// bases B, B/2, B/4 at the same index k, so consecutive threads read consecutive entries.
+template <int DIR>
+__device__ __forceinline__ float2 twb_at(const float2* __restrict__ twb, int B, int k) {
+  return twiddle<DIR>(twb + (B - 2), k);
+}
+
 template <int NS> __device__ __forceinline__ int padx(int i) {
   if constexpr (NS == 8) return pad64(i);
   else return pad16(i);
@@ -69,12 +77,11 @@ __device__ __forceinline__ void fft_reg_stage(float2 (&v)[G][8], int j, float2* 
   constexpr int REM = L / NS;
   constexpr int R = REM >= 8 ? 8 : REM;
   constexpr bool LAST = (NS * R == L);
-  constexpr int TWS = GRACE_LMAX / (NS * R);
+  constexpr int B = NS * R;            // twiddle base of this stage
   if constexpr (R == 8) {
     const int k = j & (NS - 1);
     if constexpr (NS > 1) {
-      const int m = k * TWS;
-      const float2 w1 = twiddle<DIR>(tw, m), w2 = twiddle<DIR>(tw, 2 * m), w4 = twiddle<DIR>(tw, 4 * m);
+      const float2 w1 = twb_at<DIR>(tw, B, k), w2 = twb_at<DIR>(tw, B / 2, k), w4 = twb_at<DIR>(tw, B / 4, k);
       const float2 w3 = cmul(w1, w2);
       const float2 w[8] = {w1, w1, w2, w3, w4, cmul(w1, w4), cmul(w2, w4), cmul(w3, w4)};
 #pragma unroll
@@ -108,8 +115,8 @@ __device__ __forceinline__ void fft_reg_stage(float2 (&v)[G][8], int j, float2* 
       const int k = j + b * L8;
       float2 w1 = make_float2(1.f, 0.f), w2 = w1, w3 = w1;
       if constexpr (NS > 1) {
-        w1 = twiddle<DIR>(tw, k * TWS);
-        w2 = twiddle<DIR>(tw, 2 * k * TWS);
+        w1 = twb_at<DIR>(tw, B, k);
+        w2 = twb_at<DIR>(tw, B / 2, k);
         w3 = cmul(w1, w2);
       }
 #pragma unroll
@@ -133,7 +140,7 @@ __device__ __forceinline__ void fft_reg_stage(float2 (&v)[G][8], int j, float2* 
     for (int b = 0; b < 4; ++b) {
       const int k = j + b * L8;
       float2 w1 = make_float2(1.f, 0.f);
-      if constexpr (NS > 1) w1 = twiddle<DIR>(tw, k * TWS);
+      if constexpr (NS > 1) w1 = twb_at<DIR>(tw, B, k);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         float2 a0 = v[g][b], a1 = v[g][b + 4];
@@ -146,7 +153,8 @@ __device__ __forceinline__ void fft_reg_stage(float2 (&v)[G][8], int j, float2* 
   }
 }
 
-// In-place transform of G lines held by the calling thread (see the file comment).
+// In-place transform of G lines held by the calling thread (see the file comment);
+// tw is the per-base twiddle table (twb_at).
 template <int L, int DIR, bool ZU, int G>
 __device__ __forceinline__ void fft_reg(float2 (&v)[G][8], int j, float2* sm, int gs,
                                         const float2* __restrict__ tw) {

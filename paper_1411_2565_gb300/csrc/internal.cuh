@@ -67,7 +67,8 @@ struct LaunchP {
   int TY;           // y lines per x-pass block
   int RPB;          // rows per block in the split y pass
   int TQ;           // columns per block in the split z pass
-  const float2* tw; // twiddle table, GRACE_LMAX entries
+  const float2* tw;  // twiddle table exp(-2 pi i m / GRACE_LMAX), GRACE_LMAX entries
+  const float2* twb; // per-base twiddle tables: exp(-2 pi i k / B) at twb[B - 2 + k], B = 2..GRACE_LMAX
   int pdl;          // launch with programmatic stream serialization
   float* k1;        // Heun: f(m_n), concatenated films (3 N)
   const float* hscale;  // applied-field envelope {s(t_n), s(t_n + dt)}, nullptr: constant field
