@@ -80,6 +80,24 @@ __global__ void __launch_bounds__(256, 2) kz_fast(const FilmDev* __restrict__ fi
   const int gs = TQ * LS;
   const size_t zs = (size_t)ncol;                // S[(c * nz + z) * ncol + q]
   pdl_launch_dependents();
+  {
+    // the block's tensor slots do not depend on the previous kernel: pull them into L2
+    // now so that the loads after the forward transform hit there
+    const int q0 = (unit - f.u0[UK_Z]) * TQ;
+    const int q1 = min(q0 + TQ, ncol) - 1;
+    const int kx0 = q0 / Py, kx1 = q1 / Py;
+    const int nrow = 6 * Kz;                       // (slot, kz') rows of Ky floats per kx
+    for (int idx = tid; idx < (kx1 - kx0 + 1) * nrow; idx += blockDim.x) {
+      const int kx = kx0 + idx / nrow, rr = idx % nrow;
+      const int ka = kx == kx0 ? q0 - kx * Py : 0, kb = kx == kx1 ? q1 - kx * Py : Py - 1;
+      // columns ka..kb read slots kyp in [min, max] of their mirror images
+      const int lo = (ka <= Py / 2 && kb >= Py / 2) ? (ka <= Py - kb ? ka : Py - kb)
+                                                    : (kb <= Py / 2 ? ka : Py - kb);
+      const int hi = (ka <= Py / 2 && kb >= Py / 2) ? Py / 2 : (kb <= Py / 2 ? kb : Py - ka);
+      const float* row = f.T + (size_t)kx * f.nslot * Ky + (size_t)rr * Ky;
+      for (int b = lo & ~31; b <= hi; b += 32) prefetch_l2(row + b);
+    }
+  }
   pdl_wait();
   float2 v[3][8];
 #pragma unroll

@@ -74,24 +74,16 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
   pdl_wait();
 
   if (demag) {
-    // staging S -> shared, TY rows contiguous; loads issued in batches of 8 per thread
-    constexpr int U = 8;
-    for (int base = 0; base < nst; base += U * NT) {
-      float2 buf[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = base + u * NT + tid;
-        const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
-        buf[u] = (idx < nst && y0 + t < ny) ? Sz[c * sc + (size_t)k * srow + y0 + t]
-                                             : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = base + u * NT + tid;
-        const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
-        if (idx < nst) sm[(3 * t + c) * LS + pad16(k)] = buf[u];
-      }
+    // staging S -> shared, TY rows contiguous, as asynchronous copies: every load of the
+    // block is in flight at once and none holds a register
+#pragma unroll 4
+    for (int idx = tid; idx < nst; idx += NT) {
+      const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
+      float2* dst = sm + (3 * t + c) * LS + pad16(k);
+      if (y0 + t < ny) cp_async8(dst, Sz + c * sc + (size_t)k * srow + y0 + t);
+      else *dst = make_float2(0.f, 0.f);
     }
+    cp_async_wait_all();
     __syncthreads();
     float2 v[3][8];
 #pragma unroll

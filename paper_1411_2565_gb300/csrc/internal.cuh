@@ -88,6 +88,18 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 // ... and wait until the previous grid has completed and its writes are visible.  Without
 // a programmatic launch attribute both are no-ops.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Asynchronous global -> shared copies (cp.async): no registers held while in flight;
+// cp_async_wait_all() waits for all of this thread's copies (a __syncthreads() must
+// follow before other threads read them).
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // Hint: bring one 128-byte line into L2 (L2 is coherent, so this may precede pdl_wait()).
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
