@@ -38,7 +38,9 @@ bool fast_x_supported(int Q) { return Q >= 8 && Q <= 2048; }
 int fast_x_tile(int Q) { return fastx::x_tile(Q); }
 
 size_t fast_x_smem(int Q, int TY) {
-  return (size_t)3 * TY * fastx::x_line_stride(Q, TY) * sizeof(float2) + (size_t)3 * TY * Q * sizeof(float);
+  const size_t lines = (size_t)3 * TY * fastx::x_line_stride(Q, TY) * sizeof(float2);
+  const size_t hs = (size_t)3 * TY * Q * sizeof(float);
+  return lines > hs ? lines : hs;
 }
 
 cudaError_t configure_fast_x(int Q, int TY, size_t smem) {

@@ -26,15 +26,19 @@ __host__ __device__ constexpr int x_line_stride(int Q, int TY) {
 }
 
 // Shared memory: 3 TY line buffers (x_line_stride float2 each) for staging, the Hermitian
-// merge / split and the FFT exchanges, then hs[3][TY][Q] floats holding H_demag per cell
-// and, after the update, Ms m of the new state.
+// merge / split and the FFT exchanges; hs[3][TY][Q] floats, holding H_demag per cell and,
+// after the update, Ms m of the new state, lies over the same bytes (the line buffers are
+// idle between the inverse transform and the forward one).
 // y lines per block: 256 threads where the line allows, at most 4 lines
 __host__ __device__ constexpr int x_tile(int Q) {
   return (256 / (Q / 8)) < 1 ? 1 : ((256 / (Q / 8)) > 4 ? 4 : 256 / (Q / 8));
 }
 
+// Blocks of 128 threads are bounded for 6 resident blocks (up to 80 registers; measured
+// faster than 4 despite a few spilled bytes), larger ones for 2.
 template <int Q, int TY, int MODE>
-__global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+__global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 8 == 128 ? 6 : 2)
+    kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = Q / 8;
   constexpr int NT = TY * T;
   constexpr int LS = x_line_stride(Q, TY);
@@ -50,7 +54,7 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
   float2* lines = sm + 3 * ty * LS;                              // this thread's 3 lines
-  float* hs = reinterpret_cast<float*>(sm + 3 * TY * LS);        // [3][TY][Q]
+  float* hs = reinterpret_cast<float*>(sm);                      // [3][TY][Q], over the lines
   const float* __restrict__ m = lp.mk ? lp.mk + 3 * f.cell0 : (lp.parity ? f.m1 : f.m0);
   const size_t srow = f.srow;
   const size_t sc = (size_t)nz * f.Kx * srow;                    // component stride of S
@@ -101,6 +105,8 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
     }
     __syncthreads();
     fft_reg<Q, +1, false, 3>(v, j, lines, LS, lp.twb);
+    // hs may be written at once: every read of the line buffers precedes the barrier
+    // that ends the transform's last exchange (or the one above, without exchanges)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       float2* h2 = reinterpret_cast<float2*>(hs + (c * TY + ty) * Q);
@@ -175,6 +181,7 @@ __global__ void __launch_bounds__(256, 2) kx_fast(const FilmDev* __restrict__ fi
         v[c][s + 4] = make_float2(0.f, 0.f);
       }
     }
+    __syncthreads();   // hs is read; the transform's exchanges overwrite it
     fft_reg<Q, -1, true, 3>(v, j, lines, LS, lp.twb);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
