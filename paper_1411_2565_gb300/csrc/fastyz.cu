@@ -119,21 +119,29 @@ __global__ void __launch_bounds__(256, 3) kyz_fast(const FilmDev* __restrict__ f
   __syncthreads();
 
   // tensor product: ky and its mirror PY - ky share the tensor slots (parity sign only),
-  // so one thread takes both and loads the slots once
+  // so one thread takes both and loads the slots once; the two unpaired rows, ky = 0 and
+  // the Nyquist row PY/2, form one more task, so PY/2 tasks per column keep a 256-thread
+  // block to a single round
   constexpr int NSLOT = NZ == 1 ? 4 : 6 * NZ - 2;
-  constexpr int KH = PY / 2 + 1;
-  const int ntask = KPB * KH;
+  constexpr int KH2 = PY / 2;
+  const int ntask = KPB * KH2;
   for (int p = tid; p < ntask; p += blockDim.x) {
-    const int ki = p / KH, kyp = p - ki * KH;
+    const int ki = p / KH2, kyp = p - ki * KH2;
     const int kxx = kx0 + ki;
     if (kxx >= f.Kx) continue;
-    const float* Tk = f.T + (size_t)kxx * f.nslot * f.Ky + kyp;
+    const float* Tk = f.T + (size_t)kxx * f.nslot * f.Ky;
+    float2* row = sm + (size_t)ki * NL * LS;
     float t[NSLOT];
 #pragma unroll
-    for (int s2 = 0; s2 < NSLOT; ++s2) t[s2] = __ldg(Tk + (size_t)s2 * f.Ky);
-    float2* row = sm + (size_t)ki * NL * LS;
+    for (int s2 = 0; s2 < NSLOT; ++s2) t[s2] = __ldg(Tk + (size_t)s2 * f.Ky + kyp);
     product_at<NZ, NSLOT>(row + pad16(kyp), LS, t, 1.f);
-    if (kyp > 0 && kyp < PY / 2) product_at<NZ, NSLOT>(row + pad16(PY - kyp), LS, t, -1.f);
+    if (kyp > 0) {
+      product_at<NZ, NSLOT>(row + pad16(PY - kyp), LS, t, -1.f);
+    } else {
+#pragma unroll
+      for (int s2 = 0; s2 < NSLOT; ++s2) t[s2] = __ldg(Tk + (size_t)s2 * f.Ky + PY / 2);
+      product_at<NZ, NSLOT>(row + pad16(PY / 2), LS, t, 1.f);
+    }
   }
   __syncthreads();
 #pragma unroll
