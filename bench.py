@@ -49,7 +49,30 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the block / ensemble / adjoint measurements")
+    ap.add_argument("--profile-run", default=None, choices=["film_large", "block", "film_small", "adjoint_film"],
+                    help="no measurement: take --steps plain-launch steps of this workload (for ncu)")
     return ap.parse_args()
+
+
+def profile_run(name, steps):
+    """Plain launches (no graphs) of `steps` steps, so that a profiler sees every kernel."""
+    import torch
+    import workloads
+    from paper_1411_2565_gb300 import _lib
+    from paper_1411_2565_gb300.build import build
+    from paper_1411_2565_gb300.grace import Grace
+    build()
+    w = getattr(workloads, name)()
+    f, m0 = w.films[0], w.m0[0]
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device="cuda:0",
+              options={_lib.OPT_GRAPH: 0})
+    g.set_hext(f.hext)
+    if getattr(w, "ms_field", None) is not None:
+        g.set_ms_field(torch.from_numpy(w.ms_field.reshape(-1)).cuda())
+    g.set_m(torch.from_numpy(m0.reshape(-1)).cuda())
+    g.step(steps, w.dt)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": name, "steps": steps}), flush=True)
 
 
 def dist_env():
@@ -428,6 +451,9 @@ def run_reference(args, rank, world):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.profile_run:
+        profile_run(args.profile_run, args.steps)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
