@@ -336,7 +336,14 @@ __global__ void __launch_bounds__(kThreads) k_z(const FilmDev* __restrict__ film
     buf[(c * TQ + qi) * ls + padi(z)] = v;
   }
   __syncthreads();
-  fft_lines<-1, kMaxT>(buf, Pz, 3 * TQ, ls, lp.tw, true, false);
+  // the FFT helper holds 8 kMaxT kThreads points per block: when the three components of
+  // the block's columns exceed that (one column of Pz = 4096), transform them one at a time
+  const bool by_comp = 3 * TQ * Pz > 8 * kMaxT * kThreads;
+  if (by_comp) {
+    for (int c = 0; c < 3; ++c) fft_lines<-1, kMaxT>(buf + (size_t)c * TQ * ls, Pz, TQ, ls, lp.tw, true, false);
+  } else {
+    fft_lines<-1, kMaxT>(buf, Pz, 3 * TQ, ls, lp.tw, true, false);
+  }
   for (int t = threadIdx.x; t < TQ * Pz; t += blockDim.x) {
     const int qi = t % TQ, kz = t / TQ, q = q0 + qi;
     if (q >= ncol) continue;
@@ -360,7 +367,11 @@ __global__ void __launch_bounds__(kThreads) k_z(const FilmDev* __restrict__ film
     *pz = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
   }
   __syncthreads();
-  fft_lines<+1, kMaxT>(buf, Pz, 3 * TQ, ls, lp.tw, false, true);
+  if (by_comp) {
+    for (int c = 0; c < 3; ++c) fft_lines<+1, kMaxT>(buf + (size_t)c * TQ * ls, Pz, TQ, ls, lp.tw, false, true);
+  } else {
+    fft_lines<+1, kMaxT>(buf, Pz, 3 * TQ, ls, lp.tw, false, true);
+  }
   for (int t = threadIdx.x; t < 3 * nz * TQ; t += blockDim.x) {
     const int qi = t % TQ, r = t / TQ, z = r % nz, c = r / nz;
     const int q = q0 + qi;

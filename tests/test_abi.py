@@ -41,13 +41,21 @@ def _create(lib, grid=(16, 8, 2), cell=(3e-9, 3e-9, 3e-9), Ms=8e5, A=1.3e-11, Ku
     return st, ctx
 
 
-@pytest.mark.parametrize("kw", [dict(grid=(0, 8, 2)), dict(grid=(16, 8, 4097)), dict(cell=(0, 1e-9, 1e-9)),
+@pytest.mark.parametrize("kw", [dict(grid=(0, 8, 2)), dict(grid=(16, 8, 4097)), dict(grid=(2049, 1, 1)),
+                                dict(grid=(1, 2049, 1)), dict(grid=(1, 1, 2049)), dict(grid=(-1, 1, 1)), dict(cell=(0, 1e-9, 1e-9)),
                                 dict(Ms=0.0), dict(Ms=-1.0), dict(A=-1e-11), dict(alpha=-0.1),
                                 dict(g0=0.0), dict(Ms=float("nan"))])
 def test_create_rejects_invalid_arguments(lib, kw):
     st, ctx = _create(lib, **kw)
     assert st == EINVAL
     assert not ctx.value
+
+
+def test_largest_axis_is_accepted(lib):
+    for grid in [(2048, 1, 1), (1, 2048, 1), (1, 1, 2048)]:
+        st, ctx = _create(lib, grid=grid)
+        assert st == 0
+        assert lib.grace_destroy(ctx) == 0
 
 
 def test_create_plans_workspace_and_counts_cells(lib):

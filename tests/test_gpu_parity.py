@@ -74,6 +74,23 @@ def test_heff_matches_oracle(grid, mask):
     assert np.array_equal(h, h2)
 
 
+# the largest axis (2048 cells, padded length 4096) on each path: 2048-point compile-time
+# x lines, 1024-row fused y pass (Py = 2048), 2048-point compile-time z pass (Pz = 2048),
+# and the runtime-length kernels at length 4096 along y and z
+@pytest.mark.parametrize("grid", [(2048, 3, 1), (2048, 16, 1), (16, 1024, 1), (8, 8, 1024), (3, 2048, 1),
+                                  (2, 2, 2048)])
+def test_largest_grids_match_oracle(grid):
+    f, m0 = workloads.small_film(grid, cell=(3.5e-9, 2.5e-9, 3e-9), seed=17, Ku=2e4, hext=(1.5e4, -2e4, 3e3))
+    g = make(f, m0)
+    p = params(f)
+    D = llg.Demag(grid, f.cell)
+    h = g.heff().cpu().numpy().reshape(m0.shape)
+    assert np.abs(h - llg.heff(m0, p, D)).max() / f.Ms <= TOL_H
+    g.step(1, 2e-14)
+    m1 = g.get_m().cpu().numpy().reshape(m0.shape)
+    assert np.abs(m1 - llg.euler_step(m0, p, 2e-14, D)).max() <= 2e-6
+
+
 @pytest.mark.parametrize("grid", [(24, 12, 2), (16, 8, 6), (9, 4, 1)])
 def test_heff_with_per_cell_ms_and_field(grid):
     f, m0 = workloads.small_film(grid, seed=7, Ku=1e4, hext=(1e4, 0.0, 0.0))
