@@ -84,6 +84,77 @@ __device__ __forceinline__ CellState cell_field(const FilmDev& f, unsigned mask,
   return c;
 }
 
+// cell_field for the two cells x, x + 1 of a row (x even, nx even, the film's arrays
+// 8-byte aligned): the pair's centres and y / z neighbours come in 8-byte loads and the
+// two share their x neighbours.  The arithmetic is cell_field's, term for term.
+__device__ __forceinline__ void cell_field_pair(const FilmDev& f, unsigned mask, const float* __restrict__ m,
+                                                int i, int x, int y, int z, float2 hdx, float2 hdy,
+                                                float2 hdz, float hs, CellState& ca, CellState& cb) {
+  const int N = f.ncell, nx = f.nx, ny = f.ny, nz = f.nz;
+  auto ld2 = [&](int k) { return *reinterpret_cast<const float2*>(m + k); };
+  const float2 mx = ld2(i), my = ld2(N + i), mz = ld2(2 * N + i);
+  ca.mx = mx.x; ca.my = my.x; ca.mz = mz.x;
+  cb.mx = mx.y; cb.my = my.y; cb.mz = mz.y;
+  if (f.ms_field) {
+    const float2 ms = *reinterpret_cast<const float2*>(f.ms_field + i);
+    ca.Ms = ms.x;
+    cb.Ms = ms.y;
+  } else {
+    ca.Ms = cb.Ms = f.Ms;
+  }
+  float ax = hdx.x, ay = hdy.x, az = hdz.x, bx = hdx.y, by = hdy.y, bz = hdz.y;
+  if (mask & 2u) {
+    // x: cell a has (x - 1 if any) and b; cell b has a and (x + 2 if any)
+    float pax = 0.f, pay = 0.f, paz = 0.f, pbx = 0.f, pby = 0.f, pbz = 0.f;
+    if (x > 0) { pax += m[i - 1] - mx.x; pay += m[N + i - 1] - my.x; paz += m[2 * N + i - 1] - mz.x; }
+    pax += mx.y - mx.x; pay += my.y - my.x; paz += mz.y - mz.x;
+    pbx += mx.x - mx.y; pby += my.x - my.y; pbz += mz.x - mz.y;
+    if (x + 2 < nx) { pbx += m[i + 2] - mx.y; pby += m[N + i + 2] - my.y; pbz += m[2 * N + i + 2] - mz.y; }
+    float sax = pax * f.idx2, say = pay * f.idx2, saz = paz * f.idx2;
+    float sbx = pbx * f.idx2, sby = pby * f.idx2, sbz = pbz * f.idx2;
+    // y and z: both cells' neighbours in one 8-byte load per component
+    auto axis = [&](bool lo, bool hi, int step, float id2) {
+      float qax = 0.f, qay = 0.f, qaz = 0.f, qbx = 0.f, qby = 0.f, qbz = 0.f;
+      if (lo) {
+        const float2 nxv = ld2(i - step), nyv = ld2(N + i - step), nzv = ld2(2 * N + i - step);
+        qax += nxv.x - mx.x; qay += nyv.x - my.x; qaz += nzv.x - mz.x;
+        qbx += nxv.y - mx.y; qby += nyv.y - my.y; qbz += nzv.y - mz.y;
+      }
+      if (hi) {
+        const float2 nxv = ld2(i + step), nyv = ld2(N + i + step), nzv = ld2(2 * N + i + step);
+        qax += nxv.x - mx.x; qay += nyv.x - my.x; qaz += nzv.x - mz.x;
+        qbx += nxv.y - mx.y; qby += nyv.y - my.y; qbz += nzv.y - mz.y;
+      }
+      sax = fmaf(qax, id2, sax); say = fmaf(qay, id2, say); saz = fmaf(qaz, id2, saz);
+      sbx = fmaf(qbx, id2, sbx); sby = fmaf(qby, id2, sby); sbz = fmaf(qbz, id2, sbz);
+    };
+    axis(y > 0, y < ny - 1, nx, f.idy2);
+    axis(z > 0, z < nz - 1, nx * ny, f.idz2);
+    const float cea = f.ms_field ? f.cex * __frcp_rn(ca.Ms) : f.cex_ms;
+    const float ceb = f.ms_field ? f.cex * __frcp_rn(cb.Ms) : f.cex_ms;
+    ax = fmaf(cea, sax, ax); ay = fmaf(cea, say, ay); az = fmaf(cea, saz, az);
+    bx = fmaf(ceb, sbx, bx); by = fmaf(ceb, sby, by); bz = fmaf(ceb, sbz, bz);
+  }
+  if (mask & 4u) {
+    ax = fmaf(f.ms_field ? f.can * __frcp_rn(ca.Ms) : f.can_ms, ca.mx, ax);
+    bx = fmaf(f.ms_field ? f.can * __frcp_rn(cb.Ms) : f.can_ms, cb.mx, bx);
+  }
+  if (mask & 8u) {
+    float eax = f.hx, eay = f.hy, eaz = f.hz, ebx = f.hx, eby = f.hy, ebz = f.hz;
+    if (f.h_field) {
+      const float2 hx2 = *reinterpret_cast<const float2*>(f.h_field + i);
+      const float2 hy2 = *reinterpret_cast<const float2*>(f.h_field + N + i);
+      const float2 hz2 = *reinterpret_cast<const float2*>(f.h_field + 2 * N + i);
+      eax += hx2.x; eay += hy2.x; eaz += hz2.x;
+      ebx += hx2.y; eby += hy2.y; ebz += hz2.y;
+    }
+    ax = fmaf(hs, eax, ax); ay = fmaf(hs, eay, ay); az = fmaf(hs, eaz, az);
+    bx = fmaf(hs, ebx, bx); by = fmaf(hs, eby, by); bz = fmaf(hs, ebz, bz);
+  }
+  ca.hx = ax; ca.hy = ay; ca.hz = az;
+  cb.hx = bx; cb.hy = by; cb.hz = bz;
+}
+
 __device__ __forceinline__ float3 cross3(float ax, float ay, float az, float bx, float by, float bz) {
   return make_float3(ay * bz - az * by, az * bx - ax * bz, ax * by - ay * bx);
 }

@@ -139,6 +139,45 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
     const unsigned mask =
         (MODE == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
     const float hsc = lp.hscale ? lp.hscale[MODE == XM_HEUN2 ? 1 : 0] : 1.f;
+    // even rows with 8-byte aligned arrays: cells in pairs (x, x + 1), 8-byte loads
+    const bool pairs = ((nx | f.cell0) & 1) == 0 &&
+                       ((reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(f.ms_field) |
+                         reinterpret_cast<uintptr_t>(f.h_field)) & 7) == 0;
+    if (pairs) {
+      constexpr int QP = Q / 2;
+      constexpr int U2 = 2;
+      for (int base = 0; base < TY * QP; base += U2 * NT) {
+        CellState ca[U2], cb[U2];
+        bool ok[U2];
+#pragma unroll
+        for (int u = 0; u < U2; ++u) {
+          const int idx = base + u * NT + tid;
+          const int t = idx / QP, x = 2 * (idx - t * QP), y = y0 + t;
+          ok[u] = idx < TY * QP && x < nx && y < ny;
+          if (ok[u]) {
+            const float2* hp = reinterpret_cast<const float2*>(hs + t * Q + x);
+            cell_field_pair(f, mask, m, (z * ny + y) * nx + x, x, y, z, hp[0], hp[TY * Q / 2], hp[TY * Q], hsc,
+                            ca[u], cb[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U2; ++u) {
+          const int idx = base + u * NT + tid;
+          if (idx >= TY * QP) continue;
+          const int t = idx / QP, x = 2 * (idx - t * QP), y = y0 + t;
+          float3 ra = make_float3(0.f, 0.f, 0.f), rb = ra;
+          if (ok[u]) {
+            const int i = (z * ny + y) * nx + x;
+            ra = cell_apply<MODE>(f, lp, i, ca[u]);
+            rb = cell_apply<MODE>(f, lp, i + 1, cb[u]);
+          }
+          float2* hp = reinterpret_cast<float2*>(hs + t * Q + x);
+          hp[0] = make_float2(ra.x, rb.x);
+          hp[TY * Q / 2] = make_float2(ra.y, rb.y);
+          hp[TY * Q] = make_float2(ra.z, rb.z);
+        }
+      }
+    } else {
     constexpr int U = 4;
     for (int base = 0; base < TY * Q; base += U * NT) {
       CellState cs[U];
@@ -165,6 +204,7 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
         hp[TY * Q] = r.y;
         hp[2 * TY * Q] = r.z;
       }
+    }
     }
   }
   const bool r2c = (MODE != XM_HEFF && MODE != XM_ADJ2) || (MODE == XM_HEFF && demag);
