@@ -159,8 +159,39 @@ __device__ __forceinline__ float3 cross3(float ax, float ay, float az, float bx,
   return make_float3(ay * bz - az * by, az * bx - ax * bz, ax * by - ay * bx);
 }
 
-// Writes the cell's result (H for XM_HEFF, m_{n+1} for XM_STEP) and returns Ms m of the
-// state the next spectrum is built from.
+// Eq. 3: dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)] at one cell, then the
+// renormalised update.  STEP / HEUN1: u = m + dt f (HEUN1 also returns k1 = f(m_n));
+// HEUN2 (corrector; m the predictor, mn = m_n, k1 from the predictor pass):
+// u = m_n + dt (k1 + f(m))/2.
+template <int MODE>
+__device__ __forceinline__ float3 llg_next(const FilmDev& f, const LaunchP& lp, const CellState& c, float3 k1,
+                                           float3 mn, float3& k1_out) {
+  const float mx = c.mx, my = c.my, mz = c.mz;
+  const float3 p = cross3(mx, my, mz, c.hx, c.hy, c.hz);
+  const float3 q = cross3(mx, my, mz, p.x, p.y, p.z);
+  float ux, uy, uz;
+  if (MODE == XM_HEUN2) {
+    const float hdt = 0.5f * f.llg_c * lp.dt;
+    ux = fmaf(hdt, fmaf(f.alpha, q.x, p.x), fmaf(0.5f * lp.dt, k1.x, mn.x));
+    uy = fmaf(hdt, fmaf(f.alpha, q.y, p.y), fmaf(0.5f * lp.dt, k1.y, mn.y));
+    uz = fmaf(hdt, fmaf(f.alpha, q.z, p.z), fmaf(0.5f * lp.dt, k1.z, mn.z));
+  } else {
+    const float cdt = f.llg_c * lp.dt;
+    if (MODE == XM_HEUN1)
+      k1_out = make_float3(f.llg_c * fmaf(f.alpha, q.x, p.x), f.llg_c * fmaf(f.alpha, q.y, p.y),
+                           f.llg_c * fmaf(f.alpha, q.z, p.z));
+    ux = fmaf(cdt, fmaf(f.alpha, q.x, p.x), mx);
+    uy = fmaf(cdt, fmaf(f.alpha, q.y, p.y), my);
+    uz = fmaf(cdt, fmaf(f.alpha, q.z, p.z), mz);
+  }
+  const float inv = rnorm(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+  return make_float3(ux * inv, uy * inv, uz * inv);
+}
+
+// Writes the cell's result (H for XM_HEFF, m_{n+1} for XM_STEP, the predictor and k1 for
+// XM_HEUN1, m_{n+1} for XM_HEUN2) and returns Ms m of the state the next spectrum is built
+// from.  The output m buffer is the one not read (for HEUN2 it holds m_n: each cell reads
+// only its own entry there before writing it).
 template <int MODE>
 __device__ __forceinline__ float3 cell_apply(const FilmDev& f, const LaunchP& lp, int i, const CellState& c) {
   const int N = f.ncell;
@@ -172,40 +203,66 @@ __device__ __forceinline__ float3 cell_apply(const FilmDev& f, const LaunchP& lp
     o[2 * N + i] = c.hz;
     return make_float3(c.Ms * c.mx, c.Ms * c.my, c.Ms * c.mz);
   }
-  // Eq. 3: dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)], then renormalise
-  const float mx = c.mx, my = c.my, mz = c.mz;
-  const float3 p = cross3(mx, my, mz, c.hx, c.hy, c.hz);
-  const float3 q = cross3(mx, my, mz, p.x, p.y, p.z);
   float* mo = lp.parity ? f.m0 : f.m1;
-  float ux, uy, uz;
+  float* k1p = lp.k1 + 3 * f.cell0;
+  float3 k1 = make_float3(0.f, 0.f, 0.f), mn = k1, k1o = k1;
   if (MODE == XM_HEUN2) {
-    // corrector: m_{n+1} = normalise(m_n + dt (k1 + k2)/2), k2 = f(m*) with m* the current
-    // state; m_n sits in the output buffer (each cell reads only its own entry there)
-    const float* k1 = lp.k1 + 3 * f.cell0;
-    const float hdt = 0.5f * f.llg_c * lp.dt;
-    ux = fmaf(hdt, fmaf(f.alpha, q.x, p.x), fmaf(0.5f * lp.dt, k1[i], mo[i]));
-    uy = fmaf(hdt, fmaf(f.alpha, q.y, p.y), fmaf(0.5f * lp.dt, k1[N + i], mo[N + i]));
-    uz = fmaf(hdt, fmaf(f.alpha, q.z, p.z), fmaf(0.5f * lp.dt, k1[2 * N + i], mo[2 * N + i]));
-  } else {
-    const float cdt = f.llg_c * lp.dt;
-    if (MODE == XM_HEUN1) {
-      float* k1 = lp.k1 + 3 * f.cell0;
-      k1[i] = f.llg_c * fmaf(f.alpha, q.x, p.x);
-      k1[N + i] = f.llg_c * fmaf(f.alpha, q.y, p.y);
-      k1[2 * N + i] = f.llg_c * fmaf(f.alpha, q.z, p.z);
-    }
-    ux = fmaf(cdt, fmaf(f.alpha, q.x, p.x), mx);
-    uy = fmaf(cdt, fmaf(f.alpha, q.y, p.y), my);
-    uz = fmaf(cdt, fmaf(f.alpha, q.z, p.z), mz);
+    k1 = make_float3(k1p[i], k1p[N + i], k1p[2 * N + i]);
+    mn = make_float3(mo[i], mo[N + i], mo[2 * N + i]);
   }
-  const float inv = rnorm(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
-  ux *= inv;
-  uy *= inv;
-  uz *= inv;
-  mo[i] = ux;
-  mo[N + i] = uy;
-  mo[2 * N + i] = uz;
-  return make_float3(c.Ms * ux, c.Ms * uy, c.Ms * uz);
+  const float3 u = llg_next<MODE>(f, lp, c, k1, mn, k1o);
+  if (MODE == XM_HEUN1) {
+    k1p[i] = k1o.x;
+    k1p[N + i] = k1o.y;
+    k1p[2 * N + i] = k1o.z;
+  }
+  mo[i] = u.x;
+  mo[N + i] = u.y;
+  mo[2 * N + i] = u.z;
+  return make_float3(c.Ms * u.x, c.Ms * u.y, c.Ms * u.z);
+}
+
+// cell_apply for the pair (i, i + 1) of cell_field_pair, with 8-byte loads and stores.
+template <int MODE>
+__device__ __forceinline__ void cell_apply_pair(const FilmDev& f, const LaunchP& lp, int i, const CellState& ca,
+                                                const CellState& cb, float3& ra, float3& rb) {
+  const int N = f.ncell;
+  auto st2 = [](float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); };
+  auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
+  if (MODE == XM_R2C || MODE == XM_HEFF) {
+    if (MODE == XM_HEFF) {
+      float* o = lp.out + 3 * f.cell0;
+      st2(o + i, ca.hx, cb.hx);
+      st2(o + N + i, ca.hy, cb.hy);
+      st2(o + 2 * N + i, ca.hz, cb.hz);
+    }
+    ra = make_float3(ca.Ms * ca.mx, ca.Ms * ca.my, ca.Ms * ca.mz);
+    rb = make_float3(cb.Ms * cb.mx, cb.Ms * cb.my, cb.Ms * cb.mz);
+    return;
+  }
+  float* mo = lp.parity ? f.m0 : f.m1;
+  float* k1p = lp.k1 + 3 * f.cell0;
+  float3 k1a = make_float3(0.f, 0.f, 0.f), k1b = k1a, mna = k1a, mnb = k1a, k1oa = k1a, k1ob = k1a;
+  if (MODE == XM_HEUN2) {
+    const float2 kx = ld2(k1p + i), ky = ld2(k1p + N + i), kz = ld2(k1p + 2 * N + i);
+    const float2 nx = ld2(mo + i), ny = ld2(mo + N + i), nz = ld2(mo + 2 * N + i);
+    k1a = make_float3(kx.x, ky.x, kz.x);
+    k1b = make_float3(kx.y, ky.y, kz.y);
+    mna = make_float3(nx.x, ny.x, nz.x);
+    mnb = make_float3(nx.y, ny.y, nz.y);
+  }
+  const float3 ua = llg_next<MODE>(f, lp, ca, k1a, mna, k1oa);
+  const float3 ub = llg_next<MODE>(f, lp, cb, k1b, mnb, k1ob);
+  if (MODE == XM_HEUN1) {
+    st2(k1p + i, k1oa.x, k1ob.x);
+    st2(k1p + N + i, k1oa.y, k1ob.y);
+    st2(k1p + 2 * N + i, k1oa.z, k1ob.z);
+  }
+  st2(mo + i, ua.x, ub.x);
+  st2(mo + N + i, ua.y, ub.y);
+  st2(mo + 2 * N + i, ua.z, ub.z);
+  ra = make_float3(ca.Ms * ua.x, ca.Ms * ua.y, ca.Ms * ua.z);
+  rb = make_float3(cb.Ms * ub.x, cb.Ms * ub.y, cb.Ms * ub.z);
 }
 
 // First pointwise half of the adjoint of one step m' = normalise(m + dt f(m, H(m))):

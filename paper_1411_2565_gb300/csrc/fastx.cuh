@@ -139,10 +139,11 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
     const unsigned mask =
         (MODE == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
     const float hsc = lp.hscale ? lp.hscale[MODE == XM_HEUN2 ? 1 : 0] : 1.f;
-    // even rows with 8-byte aligned arrays: cells in pairs (x, x + 1), 8-byte loads
+    // even rows with 8-byte aligned arrays (the caller's H output included): cells in
+    // pairs (x, x + 1), 8-byte loads and stores
     const bool pairs = ((nx | f.cell0) & 1) == 0 &&
                        ((reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(f.ms_field) |
-                         reinterpret_cast<uintptr_t>(f.h_field)) & 7) == 0;
+                         reinterpret_cast<uintptr_t>(f.h_field) | reinterpret_cast<uintptr_t>(lp.out)) & 7) == 0;
     if (pairs) {
       constexpr int QP = Q / 2;
       constexpr int U2 = 2;
@@ -168,8 +169,7 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
           float3 ra = make_float3(0.f, 0.f, 0.f), rb = ra;
           if (ok[u]) {
             const int i = (z * ny + y) * nx + x;
-            ra = cell_apply<MODE>(f, lp, i, ca[u]);
-            rb = cell_apply<MODE>(f, lp, i + 1, cb[u]);
+            cell_apply_pair<MODE>(f, lp, i, ca[u], cb[u], ra, rb);
           }
           float2* hp = reinterpret_cast<float2*>(hs + t * Q + x);
           hp[0] = make_float2(ra.x, rb.x);
@@ -229,24 +229,22 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
       for (int r = 0; r < 8; ++r) lines[c * LS + pad16(j + r * T)] = v[c][r];
   }
   __syncthreads();
-  // split and store, TY rows of S contiguous:
-  // X_k = (Z_k + conj Z_{Q-k})/2 - (i/2) W^k (Z_k - conj Z_{Q-k}), X_Q = Re Z_0 - Im Z_0
-  for (int idx = tid; idx < nst; idx += NT) {
-    const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
+  // split and store, TY rows of S contiguous; one pass over k = 0..Q/2 gives both X_k and
+  // X_{Q-k} from the same Z_k, Z_{Q-k}: with a = Z_k + conj Z_{Q-k}, b = Z_k - conj Z_{Q-k},
+  // c = W^k b (W = exp(-2 pi i / 2Q), W^{Q-k} = -conj W^k):
+  //   X_k = (a - i c)/2,  X_{Q-k} = (conj a - i conj c)/2   (k = 0 gives X_0 and X_Q)
+  constexpr int QH = Q / 2 + 1;
+  for (int idx = tid; idx < 3 * QH * TY; idx += NT) {
+    const int t = idx % TY, r = idx / TY, k = r % QH, c = r / QH;
     const int yy = y0 + t;
     if (yy >= ny) continue;
     const float2* ln = sm + (3 * t + c) * LS;
-    const float2 zk = ln[pad16(k & (Q - 1))];
-    float2 xo;
-    if (k == Q) {
-      xo = make_float2(zk.x - zk.y, 0.f);
-    } else {
-      const float2 zq = ln[pad16((Q - k) & (Q - 1))];
-      const float2 a = cadd(zk, cconj(zq)), b = csub(zk, cconj(zq));
-      const float2 wb = cmul(twb_at<-1>(lp.twb, 2 * Q, k), b);
-      xo = make_float2(0.5f * (a.x + wb.y), 0.5f * (a.y - wb.x));
-    }
-    Sz[c * sc + (size_t)k * srow + yy] = xo;
+    const float2 zk = ln[pad16(k)], zq = ln[pad16((Q - k) & (Q - 1))];
+    const float2 a = cadd(zk, cconj(zq)), b = csub(zk, cconj(zq));
+    const float2 wb = cmul(twb_at<-1>(lp.twb, 2 * Q, k), b);
+    float2* dst = Sz + c * sc + yy;
+    dst[(size_t)k * srow] = make_float2(0.5f * (a.x + wb.y), 0.5f * (a.y - wb.x));
+    if (k != Q / 2) dst[(size_t)(Q - k) * srow] = make_float2(0.5f * (a.x - wb.y), -0.5f * (a.y + wb.x));
   }
 }
 

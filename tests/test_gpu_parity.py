@@ -104,6 +104,34 @@ def test_heff_with_per_cell_ms_and_field(grid):
     assert np.abs(h - ref).max() / ms.min() <= TOL_H
 
 
+def test_unaligned_caller_buffers_take_the_single_cell_path():
+    """Per-cell Ms, per-cell field and the H output at odd float offsets (4-byte aligned
+    only): the x pass falls back from paired 8-byte accesses to single cells, with the same
+    arithmetic, so H_eff and a step are bit-identical to the aligned run and match the oracle."""
+    f, m0 = workloads.small_film((24, 12, 2), seed=71, Ku=1e4, hext=(1e4, 0.0, 0.0))
+    shape = f.shape_zyx
+    n = int(np.prod(shape))
+    ms = (6e5 + 4e5 * workloads.uniform(72, n)).astype(np.float32)
+    hf = (3e4 * (2 * workloads.uniform(73, 3 * n) - 1)).astype(np.float32)
+    results = []
+    for off in (0, 1):
+        ms_buf = torch.zeros(n + 1, device=DEV)
+        ms_buf[off:off + n] = torch.from_numpy(ms).to(DEV)
+        hf_buf = torch.zeros(3 * n + 1, device=DEV)
+        hf_buf[off:off + 3 * n] = torch.from_numpy(hf).to(DEV)
+        out_buf = torch.zeros(3 * n + 1, device=DEV)
+        g = make(f, m0)
+        g.set_ms_field(ms_buf[off:off + n])
+        g.set_hext_field(hf_buf[off:off + 3 * n])
+        h = g.heff(out=out_buf[off:off + 3 * n]).cpu().numpy().copy()
+        g.step(3, 1e-14)
+        results.append((h, g.get_m().cpu().numpy()))
+    assert np.array_equal(results[0][0], results[1][0])
+    assert np.array_equal(results[0][1], results[1][1])
+    ref = llg.heff(m0, params(f, ms=ms.reshape(shape), hfield=hf.reshape((3,) + shape)))
+    assert np.abs(results[1][0].reshape(m0.shape) - ref).max() / ms.min() <= TOL_H
+
+
 @pytest.mark.parametrize("grid", [(24, 12, 2), (16, 8, 6), (1, 1, 1)])
 def test_single_step_matches_oracle(grid):
     f, m0 = workloads.small_film(grid, seed=3, Ku=1e4, alpha=0.2, hext=(0, 2e4, 0))
