@@ -26,7 +26,7 @@ template <bool WEIGHTED>
 __device__ __forceinline__ float3 laplacian(const FilmDev& f, const float* __restrict__ a, int i, int x,
                                             int y, int z, float wi, float cw) {
   const int nx = f.nx, ny = f.ny, nz = f.nz, N = f.ncell;
-  auto w = [&](int j) { return WEIGHTED ? cw / cell_ms(f, j) : 1.f; };
+  auto w = [&](int j) { return WEIGHTED ? cw * __frcp_rn(cell_ms(f, j)) : 1.f; };
   const float ax0 = wi * a[i], ay0 = wi * a[N + i], az0 = wi * a[2 * N + i];
   float sx = 0.f, sy = 0.f, sz = 0.f;
   float bx = 0.f, by = 0.f, bz = 0.f;
@@ -273,14 +273,42 @@ __device__ __forceinline__ void cell_apply_pair(const FilmDev& f, const LaunchP&
 //                 + (2Ku/(mu0 Ms)) nu_x x                          (f and H_anis terms)
 // Accumulates dL/dH_ext += nu and the local part of dL/dMs, -nu.(H_exch + H_anis)/Ms;
 // stores lambda_part and nu and returns nu (unit weight), the next demag input.
-__device__ __forceinline__ float3 adj1_cell(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
-                                            int i, int x, int y, int z, float hdx, float hdy, float hdz) {
+// Split into the cell's loads (adj1_load) and the rest (adj1_finish) so that callers can
+// put several cells' loads in flight before using any.
+struct Adj1In {
+  CellState loc;          // m, Ms and H_exch + H_anis
+  float ex, ey, ez;       // H_ext
+  float lx, ly, lz;       // lambda_{k+1}
+};
+
+__device__ __forceinline__ Adj1In adj1_load(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
+                                            int i, int x, int y, int z) {
+  const int N = f.ncell;
+  Adj1In a;
+  a.loc = cell_field(f, 2u | 4u, m, i, x, y, z, 0.f, 0.f, 0.f);
+  a.ex = f.hx;
+  a.ey = f.hy;
+  a.ez = f.hz;
+  if (f.h_field) {
+    a.ex += f.h_field[i];
+    a.ey += f.h_field[N + i];
+    a.ez += f.h_field[2 * N + i];
+  }
+  const float* li = lp.adj_lam_in + 3 * f.cell0;
+  a.lx = li[i];
+  a.ly = li[N + i];
+  a.lz = li[2 * N + i];
+  return a;
+}
+
+__device__ __forceinline__ float3 adj1_finish(const FilmDev& f, const LaunchP& lp, int i, const Adj1In& in,
+                                              float hdx, float hdy, float hdz) {
   const int N = f.ncell;
   const long long o = 3 * f.cell0;
-  const CellState loc = cell_field(f, 2u | 4u, m, i, x, y, z, 0.f, 0.f, 0.f);   // H_exch + H_anis
-  const CellState ext = cell_field(f, 8u, m, i, x, y, z, 0.f, 0.f, 0.f);        // H_ext
-  const float mx = loc.mx, my = loc.my, mz = loc.mz, Ms = loc.Ms;
-  const float Hx = hdx + loc.hx + ext.hx, Hy = hdy + loc.hy + ext.hy, Hz = hdz + loc.hz + ext.hz;
+  const CellState& loc = in.loc;
+  const float mx = loc.mx, my = loc.my, mz = loc.mz;
+  const float rms = __frcp_rn(loc.Ms);
+  const float Hx = hdx + loc.hx + in.ex, Hy = hdy + loc.hy + in.ey, Hz = hdz + loc.hz + in.ez;
   const float3 p = cross3(mx, my, mz, Hx, Hy, Hz);               // m x H
   const float3 q = cross3(mx, my, mz, p.x, p.y, p.z);            // m x (m x H)
   const float cdt = f.llg_c * lp.dt;                             // -dt c
@@ -289,8 +317,7 @@ __device__ __forceinline__ float3 adj1_cell(const FilmDev& f, const LaunchP& lp,
   const float uz = fmaf(cdt, fmaf(f.alpha, q.z, p.z), mz);
   const float inv = rnorm(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));   // as in the forward step
   const float m1x = ux * inv, m1y = uy * inv, m1z = uz * inv;
-  const float* li = lp.adj_lam_in + o;
-  const float lx = li[i], ly = li[N + i], lz = li[2 * N + i];
+  const float lx = in.lx, ly = in.ly, lz = in.lz;
   const float d = m1x * lx + m1y * ly + m1z * lz;
   const float mux = (lx - m1x * d) * inv, muy = (ly - m1y * d) * inv, muz = (lz - m1z * d) * inv;
   const float3 a = cross3(mx, my, mz, mux, muy, muz);            // m x mu
@@ -304,7 +331,7 @@ __device__ __forceinline__ float3 adj1_cell(const FilmDev& f, const LaunchP& lp,
   float lpx = mux + dtc * (-t1.x + f.alpha * (t3.x - t2.x));
   const float lpy = muy + dtc * (-t1.y + f.alpha * (t3.y - t2.y));
   const float lpz = muz + dtc * (-t1.z + f.alpha * (t3.z - t2.z));
-  lpx = fmaf(f.can / Ms, nx_, lpx);
+  lpx = fmaf(f.can * rms, nx_, lpx);
   float* lp_ = lp.adj_lam_part + o;
   lp_[i] = lpx;
   lp_[N + i] = lpy;
@@ -319,34 +346,68 @@ __device__ __forceinline__ float3 adj1_cell(const FilmDev& f, const LaunchP& lp,
     g[N + i] += ny_;
     g[2 * N + i] += nz_;
   }
-  if (lp.adj_g_ms) lp.adj_g_ms[f.cell0 + i] -= (nx_ * loc.hx + ny_ * loc.hy + nz_ * loc.hz) / Ms;
+  if (lp.adj_g_ms) lp.adj_g_ms[f.cell0 + i] -= (nx_ * loc.hx + ny_ * loc.hy + nz_ * loc.hz) * rms;
   return make_float3(nx_, ny_, nz_);
+}
+
+__device__ __forceinline__ float3 adj1_cell(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
+                                            int i, int x, int y, int z, float hdx, float hdy, float hdz) {
+  return adj1_finish(f, lp, i, adj1_load(f, lp, m, i, x, y, z), hdx, hdy, hdz);
 }
 
 // Second pointwise half: with D = -N * nu (the demag convolution of nu, unit weights),
 //   lambda = lambda_part + Ms D + L(C nu),  C = diag(2A/(mu0 Ms_i))   (D and exchange terms)
 //   dL/dMs += m . D
-__device__ __forceinline__ void adj2_cell(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
-                                          int i, int x, int y, int z, float dx, float dy, float dz) {
+// Loads (with the exchange term, which is all loads) in adj2_load, stores in adj2_finish.
+struct Adj2In {
+  float Ms;
+  float3 l;                // L(C nu) at the cell
+  float px, py, pz;        // lambda_part
+  float mx, my, mz;        // m (for dL/dMs)
+};
+
+__device__ __forceinline__ Adj2In adj2_load(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
+                                            int i, int x, int y, int z) {
   const int N = f.ncell;
   const long long o = 3 * f.cell0;
-  const float Ms = cell_ms(f, i);
+  Adj2In a;
+  a.Ms = cell_ms(f, i);
   const float* nu = lp.adj_nu + o;
-  float3 l = make_float3(0.f, 0.f, 0.f);
+  a.l = make_float3(0.f, 0.f, 0.f);
   if (f.cex != 0.f) {
-    if (f.ms_field) l = laplacian<true>(f, nu, i, x, y, z, f.cex / Ms, f.cex);
+    const float ci = f.cex * __frcp_rn(a.Ms);
+    if (f.ms_field) a.l = laplacian<true>(f, nu, i, x, y, z, ci, f.cex);
     else {
-      l = laplacian<false>(f, nu, i, x, y, z, 1.f, 0.f);
-      const float c = f.cex / Ms;
-      l = make_float3(c * l.x, c * l.y, c * l.z);
+      const float3 l = laplacian<false>(f, nu, i, x, y, z, 1.f, 0.f);
+      a.l = make_float3(ci * l.x, ci * l.y, ci * l.z);
     }
   }
   const float* lpart = lp.adj_lam_part + o;
-  float* lo = lp.adj_lam_out + o;
-  lo[i] = lpart[i] + fmaf(Ms, dx, l.x);
-  lo[N + i] = lpart[N + i] + fmaf(Ms, dy, l.y);
-  lo[2 * N + i] = lpart[2 * N + i] + fmaf(Ms, dz, l.z);
-  if (lp.adj_g_ms) lp.adj_g_ms[f.cell0 + i] += m[i] * dx + m[N + i] * dy + m[2 * N + i] * dz;
+  a.px = lpart[i];
+  a.py = lpart[N + i];
+  a.pz = lpart[2 * N + i];
+  a.mx = a.my = a.mz = 0.f;
+  if (lp.adj_g_ms) {
+    a.mx = m[i];
+    a.my = m[N + i];
+    a.mz = m[2 * N + i];
+  }
+  return a;
+}
+
+__device__ __forceinline__ void adj2_finish(const FilmDev& f, const LaunchP& lp, int i, const Adj2In& a, float dx,
+                                            float dy, float dz) {
+  const int N = f.ncell;
+  float* lo = lp.adj_lam_out + 3 * f.cell0;
+  lo[i] = a.px + fmaf(a.Ms, dx, a.l.x);
+  lo[N + i] = a.py + fmaf(a.Ms, dy, a.l.y);
+  lo[2 * N + i] = a.pz + fmaf(a.Ms, dz, a.l.z);
+  if (lp.adj_g_ms) lp.adj_g_ms[f.cell0 + i] += a.mx * dx + a.my * dy + a.mz * dz;
+}
+
+__device__ __forceinline__ void adj2_cell(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
+                                          int i, int x, int y, int z, float dx, float dy, float dz) {
+  adj2_finish(f, lp, i, adj2_load(f, lp, m, i, x, y, z), dx, dy, dz);
 }
 
 }  // namespace grace

@@ -11,6 +11,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cell.cuh"
 #include "fftreg.cuh"
 #include "internal.cuh"
@@ -119,19 +121,40 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
   __syncthreads();
 
   if constexpr (MODE == XM_ADJ1 || MODE == XM_ADJ2) {
-    // adjoint halves: H_demag(m_k) -> lambda_part, nu (R2C of nu follows), or D(nu) -> lambda_k
-    for (int idx = tid; idx < TY * Q; idx += NT) {
-      const int t = idx / Q, x = idx - t * Q, y = y0 + t;
-      float* hp = hs + t * Q + x;
-      float3 r = make_float3(0.f, 0.f, 0.f);
-      if (x < nx && y < ny) {
-        const int i = (z * ny + y) * nx + x;
-        if (MODE == XM_ADJ1) r = adj1_cell(f, lp, m, i, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q]);
-        else adj2_cell(f, lp, m, i, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q]);
+    // adjoint halves: H_demag(m_k) -> lambda_part, nu (R2C of nu follows), or D(nu) -> lambda_k;
+    // the loads of UA cells are issued before any of them is finished
+    using AdjIn = std::conditional_t<MODE == XM_ADJ1, Adj1In, Adj2In>;
+    constexpr int UA = 4;
+    for (int base = 0; base < TY * Q; base += UA * NT) {
+      AdjIn in[UA];
+      bool ok[UA];
+#pragma unroll
+      for (int u = 0; u < UA; ++u) {
+        const int idx = base + u * NT + tid;
+        const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+        ok[u] = idx < TY * Q && x < nx && y < ny;
+        if (ok[u]) {
+          const int i = (z * ny + y) * nx + x;
+          if constexpr (MODE == XM_ADJ1) in[u] = adj1_load(f, lp, m, i, x, y, z);
+          else in[u] = adj2_load(f, lp, m, i, x, y, z);
+        }
       }
-      hp[0] = r.x;
-      hp[TY * Q] = r.y;
-      hp[2 * TY * Q] = r.z;
+#pragma unroll
+      for (int u = 0; u < UA; ++u) {
+        const int idx = base + u * NT + tid;
+        if (idx >= TY * Q) continue;
+        const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+        float* hp = hs + t * Q + x;
+        float3 r = make_float3(0.f, 0.f, 0.f);
+        if (ok[u]) {
+          const int i = (z * ny + y) * nx + x;
+          if constexpr (MODE == XM_ADJ1) r = adj1_finish(f, lp, i, in[u], hp[0], hp[TY * Q], hp[2 * TY * Q]);
+          else adj2_finish(f, lp, i, in[u], hp[0], hp[TY * Q], hp[2 * TY * Q]);
+        }
+        hp[0] = r.x;
+        hp[TY * Q] = r.y;
+        hp[2 * TY * Q] = r.z;
+      }
     }
   } else {
   // cell update, one thread per cell of the TY x Q tile (x >= nx, y >= ny give zeros);
