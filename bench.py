@@ -82,6 +82,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Units processed by all ranks per second of the slowest rank (replicas: weak scaling)."""
+    return units_per_rank * world * steps / seconds
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -239,14 +255,9 @@ def run_grace(args, rank, world, local):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ncell = f.ncells
-    value = ncell * world * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(ncell, world, args.steps, total_ms * 1e-3)
 
     # per-kernel durations: the same flushed single steps again, with an event pair around
     # every kernel (the events separate the kernels, so this pass is not the headline)
@@ -289,13 +300,8 @@ def run_grace(args, rank, world, local):
         g.step(1, w.dt)
         g.get_m_host(ptr_out)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": ncell * world * args.e2e_steps / t_e2e, "unit": UNIT,
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": whole_job_rate(ncell, world, args.e2e_steps, t_e2e), "unit": UNIT,
            "h2d_bytes_per_step": 12 * ncell, "d2h_bytes_per_step": 12 * ncell,
            "steps": args.e2e_steps, "path": "grace_set_m_host + grace_step(1) + grace_get_m_host"}
 
