@@ -407,7 +407,48 @@ def extra_workloads(dev):
                       "fwd_plus_bwd_ms_per_step": (t_f + t_b) / n * 1e3,
                       "method": "forward steps, then grace_backward with checkpoints every 64 "
                                 "(re-computes the forward inside)"}
+    del g
+    out["cufft_demag_comparison"] = cufft_demag_comparison(dev, flush)
     return out
+
+
+def cufft_demag_comparison(dev, flush, reps=20):
+    """Timed comparison only (not the product path): the film_large demag convolution done
+    with the vendor FFT through torch.fft on the same zero-padded grid, FP32: R2C of the
+    three padded components, the 6-component symmetric tensor product, C2R and crop.
+    The tensor values are placeholders of the right shape (timing does not depend on them)."""
+    import torch
+
+    import workloads
+    w = workloads.film_large()
+    f = w.films[0]
+    nx, ny, nz = f.grid
+    Px, Py, Pz = (1 << (2 * n - 1 - 1).bit_length() if n > 1 else 1 for n in (nx, ny, nz))
+    m = torch.zeros(3, Pz, Py, Px, device=dev)
+    m[:, :nz, :ny, :nx] = torch.randn(3, nz, ny, nx, device=dev)
+    T = torch.randn(6, Pz, Py, Px // 2 + 1, device=dev)
+
+    def conv():
+        X = torch.fft.rfftn(m, dim=(1, 2, 3))
+        H = torch.stack([T[0] * X[0] + T[3] * X[1] + T[4] * X[2],
+                         T[3] * X[0] + T[1] * X[1] + T[5] * X[2],
+                         T[4] * X[0] + T[5] * X[1] + T[2] * X[2]])
+        h = torch.fft.irfftn(H, s=(Pz, Py, Px), dim=(1, 2, 3))
+        return h[:, :nz, :ny, :nx].contiguous()
+
+    conv()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        conv()
+        b.record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+    return {"workload": w.name, "padded": [Px, Py, Pz], "ms_per_demag": round(ms, 4),
+            "equivalent_cell_steps_per_s": f.ncells / (ms * 1e-3),
+            "method": "torch.fft.rfftn / irfftn (vendor FFT) + elementwise tensor product, FP32, "
+                      f"L2 flushed before each of {reps} evaluations; demag only, no exchange or step"}
 
 
 def cpu_baseline(w, seconds):
