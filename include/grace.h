@@ -131,9 +131,15 @@ int grace_bind(grace_ctx *ctx, void *dev_ws, size_t bytes, void *cuda_stream);
 int grace_set_m(grace_ctx *ctx, const float *dev_m);
 int grace_get_m(const grace_ctx *ctx, float *dev_m);
 /* Host-memory variants: the copy is queued on the bound stream; grace_get_m_host
- * synchronises the stream before returning, so host_m is valid on return. */
+ * synchronises the stream before returning, so host_m is valid on return.  With
+ * page-locked host buffers the copies are asynchronous DMA. */
 int grace_set_m_host(grace_ctx *ctx, const float *host_m);
 int grace_get_m_host(grace_ctx *ctx, float *host_m);
+/* grace_get_m_host without the synchronisation: the copy is only queued, host_m (which
+ * should be page-locked) is valid once the bound stream has passed this point (a stream
+ * or event synchronisation by the caller).  Lets a caller keep several handles, on
+ * several streams, copying while others compute. */
+int grace_get_m_host_async(grace_ctx *ctx, float *host_m);
 
 /* Uniform applied field H_ext (A/m), Eq. 1 Zeeman term; all films, or one film. */
 int grace_set_hext(grace_ctx *ctx, const double h_Apm[3]);

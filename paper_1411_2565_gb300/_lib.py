@@ -32,6 +32,7 @@ SIGNATURES = {
     "grace_get_m": (_I, [_P, _P]),
     "grace_set_m_host": (_I, [_P, _P]),
     "grace_get_m_host": (_I, [_P, _P]),
+    "grace_get_m_host_async": (_I, [_P, _P]),
     "grace_set_hext": (_I, [_P, _DP]),
     "grace_set_film_hext": (_I, [_P, _I, _DP]),
     "grace_set_hext_field": (_I, [_P, _P]),

@@ -807,6 +807,16 @@ int grace_get_m_host(grace_ctx* c, float* host_m) {
   return GRACE_OK;
 }
 
+int grace_get_m_host_async(grace_ctx* c, float* host_m) {
+  int st = ready(c, true);
+  if (st) return st;
+  if (!host_m) return fail(c, GRACE_EINVAL, "m pointer is NULL");
+  const float* src = reinterpret_cast<const float*>(c->ws + c->o_run + (c->parity ? c->o_m1 : c->o_m0));
+  GRACE_CUDA(c, cudaMemcpyAsync(host_m, src, (size_t)3 * c->ncell * sizeof(float),
+                                cudaMemcpyDeviceToHost, c->stream));
+  return GRACE_OK;
+}
+
 int grace_set_hext(grace_ctx* c, const double h[3]) {
   if (!c || !h) return GRACE_EINVAL;
   for (size_t i = 0; i < c->films.size(); ++i) {

@@ -69,10 +69,15 @@ class _Base:
         check(self._L.grace_set_m_host(self.ctx, a.ctypes.data), "grace_set_m_host", self.ctx)
         self._keep["m_host"] = a   # the copy is queued; keep the buffer alive
 
-    def get_m_host(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+    def get_m_host(self, out: Optional[np.ndarray] = None, wait: bool = True) -> np.ndarray:
+        """Copy m to host memory; with wait=False the copy is only queued on the handle's
+        stream (grace_get_m_host_async): `out` (page-locked) is valid after a stream sync."""
         if out is None:
             out = np.empty(3 * self.ncell, dtype=np.float32)
-        check(self._L.grace_get_m_host(self.ctx, out.ctypes.data), "grace_get_m_host", self.ctx)
+        if wait:
+            check(self._L.grace_get_m_host(self.ctx, out.ctypes.data), "grace_get_m_host", self.ctx)
+        else:
+            check(self._L.grace_get_m_host_async(self.ctx, out.ctypes.data), "grace_get_m_host_async", self.ctx)
         return out
 
     # -- parameters ---------------------------------------------------------------

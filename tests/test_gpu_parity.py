@@ -282,3 +282,31 @@ def test_adjoint_film_forward_4096_steps():
     mo = llg.run(m0, params(f, ms=w.ms_field), w.dt, w.steps)
     d = np.abs(mg.reshape(3, -1).mean(1) - mo.reshape(3, -1).mean(1)).max()
     assert d <= 1e-4, d
+
+
+def test_async_host_copies_on_two_streams():
+    """grace_get_m_host_async on two handles bound to two streams, steps alternating as in
+    the end-to-end measurement: each result equals the synchronous path's."""
+    Grace, _ = _grace()
+    f, m0 = workloads.small_film((64, 16, 2), seed=81, alpha=0.3, hext=(1e4, 0.0, 0.0))
+    ref = make(f, m0)
+    ref.step(1, 1e-14)
+    expect = ref.get_m_host()
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    hs = [Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=DEV, stream=s) for s in streams]
+    host_in = torch.from_numpy(m0.reshape(-1).copy()).pin_memory()
+    outs = [torch.zeros(3 * f.ncells).pin_memory() for _ in range(2)]
+    for k in range(6):
+        i = k & 1
+        streams[i].synchronize()
+        if k >= 2:
+            assert np.array_equal(outs[i].numpy(), expect)
+        outs[i].zero_()
+        hs[i].set_hext(f.hext)
+        hs[i].set_m_host(host_in.numpy())
+        hs[i].step(1, 1e-14)
+        hs[i].get_m_host(outs[i].numpy(), wait=False)
+    for s in streams:
+        s.synchronize()
+    for o in outs:
+        assert np.array_equal(o.numpy(), expect)
