@@ -36,16 +36,34 @@ __host__ __device__ constexpr int x_tile(int Q) {
   return (256 / (Q / 8)) < 1 ? 1 : ((256 / (Q / 8)) > 4 ? 4 : 256 / (Q / 8));
 }
 
-// Blocks of 128 threads are bounded for 6 resident blocks (up to 80 registers; measured
-// faster than 4 despite a few spilled bytes), larger ones for 2.
+// Threads per block: TY Q/8 transform the lines.  The adjoint modes, whose per-cell work
+// dominates, add three helper threads per transforming thread when the transforming
+// threads fill one or two whole warps: the helpers share the staging, the cell update
+// and the split, and only keep step with the transforms' barriers.
+__host__ __device__ constexpr bool x_helpers(int Q, int TY, int MODE) {
+  return (MODE == XM_ADJ1 || MODE == XM_ADJ2) && (TY * Q / 8) % 32 == 0 && TY * Q / 8 <= 64;
+}
+__host__ __device__ constexpr int x_threads(int Q, int TY, int MODE) {
+  return x_helpers(Q, TY, MODE) ? 4 * (TY * Q / 8) : TY * Q / 8;
+}
+// Resident blocks the register bound aims at: 128-thread tiles 6 (up to 80 registers;
+// measured faster than 4 despite a few spilled bytes), blocks with helpers 512 threads per
+// SM in all, others 2.
+__host__ __device__ constexpr int x_min_blocks(int Q, int TY, int MODE) {
+  return x_helpers(Q, TY, MODE) ? 512 / x_threads(Q, TY, MODE) : (TY * Q / 8 == 128 ? 6 : 2);
+}
+
 template <int Q, int TY, int MODE>
-__global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 8 == 128 ? 6 : 2)
+__global__ void __launch_bounds__(x_threads(Q, TY, MODE) < 256 ? x_threads(Q, TY, MODE) : 256,
+                                  x_min_blocks(Q, TY, MODE))
     kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = Q / 8;
-  constexpr int NT = TY * T;
+  constexpr int NT = TY * T;                      // transforming threads
+  constexpr int NTB = x_threads(Q, TY, MODE);     // all threads of the block
   constexpr int LS = x_line_stride(Q, TY);
   const int tid = threadIdx.x;
   const int j = tid % T, ty = tid / T;
+  const bool fft_thread = NTB == NT || tid < NT;  // helpers are whole warps past the first NT
   const int unit = blockIdx.x;
   const FilmDev& f = films[find_film(films, lp.nfilms, UK_X, unit)];
   const int nx = f.nx, ny = f.ny, nz = f.nz;
@@ -71,7 +89,7 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
     // this block's rows of m are not written by the previous kernel (y pass)
     const int rows = 3 * min(TY, ny - y0);
     const int lines_per_row = (nx * (int)sizeof(float) + 127) / 128;
-    for (int idx = tid; idx < rows * lines_per_row; idx += NT) {
+    for (int idx = tid; idx < rows * lines_per_row; idx += NTB) {
       const int r = idx / lines_per_row, l = idx - r * lines_per_row;
       const int c = r / min(TY, ny - y0), t = r - c * min(TY, ny - y0);
       prefetch_l2(reinterpret_cast<const char*>(m + (size_t)c * f.ncell + (size_t)(z * ny + y0 + t) * nx) + l * 128);
@@ -83,7 +101,7 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
     // staging S -> shared, TY rows contiguous, as asynchronous copies: every load of the
     // block is in flight at once and none holds a register
 #pragma unroll 4
-    for (int idx = tid; idx < nst; idx += NT) {
+    for (int idx = tid; idx < nst; idx += NTB) {
       const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
       float2* dst = sm + (3 * t + c) * LS + pad16(k);
       if (y0 + t < ny) cp_async8(dst, Sz + c * sc + (size_t)k * srow + y0 + t);
@@ -92,31 +110,37 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
     cp_async_wait_all();
     __syncthreads();
     float2 v[3][8];
+    if (fft_thread) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      // C_k = (X_k + conj X_{Q-k}) + i W^{-k} (X_k - conj X_{Q-k})
-      const int k = j + r * T;
-      const float2 w = twb_at<+1>(lp.twb, 2 * Q, k);   // W^{-k}, P = 2Q
+      for (int r = 0; r < 8; ++r) {
+        // C_k = (X_k + conj X_{Q-k}) + i W^{-k} (X_k - conj X_{Q-k})
+        const int k = j + r * T;
+        const float2 w = twb_at<+1>(lp.twb, 2 * Q, k);   // W^{-k}, P = 2Q
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float2 xk = lines[c * LS + pad16(k)], xq = lines[c * LS + pad16(Q - k)];
-        const float2 a = cadd(xk, cconj(xq)), b = csub(xk, cconj(xq));
-        const float2 wb = cmul(w, b);
-        v[c][r] = make_float2(a.x - wb.y, a.y + wb.x);
+        for (int c = 0; c < 3; ++c) {
+          const float2 xk = lines[c * LS + pad16(k)], xq = lines[c * LS + pad16(Q - k)];
+          const float2 a = cadd(xk, cconj(xq)), b = csub(xk, cconj(xq));
+          const float2 wb = cmul(w, b);
+          v[c][r] = make_float2(a.x - wb.y, a.y + wb.x);
+        }
       }
     }
     __syncthreads();
-    fft_reg<Q, +1, false, 3>(v, j, lines, LS, lp.twb);
-    // hs may be written at once: every read of the line buffers precedes the barrier
-    // that ends the transform's last exchange (or the one above, without exchanges)
+    if (fft_thread) {
+      fft_reg<Q, +1, false, 3>(v, j, lines, LS, lp.twb);
+      // hs may be written at once: every read of the line buffers precedes the barrier
+      // that ends the transform's last exchange (or the one above, without exchanges)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float2* h2 = reinterpret_cast<float2*>(hs + (c * TY + ty) * Q);
+      for (int c = 0; c < 3; ++c) {
+        float2* h2 = reinterpret_cast<float2*>(hs + (c * TY + ty) * Q);
 #pragma unroll
-      for (int s = 0; s < 4; ++s) h2[j + s * T] = v[c][s];     // H at cells 2n, 2n+1
+        for (int s = 0; s < 4; ++s) h2[j + s * T] = v[c][s];     // H at cells 2n, 2n+1
+      }
+    } else {
+      fft_reg_barriers<Q>();
     }
   } else {
-    for (int idx = tid; idx < 3 * TY * Q; idx += NT) hs[idx] = 0.f;
+    for (int idx = tid; idx < 3 * TY * Q; idx += NTB) hs[idx] = 0.f;
   }
   __syncthreads();
 
@@ -125,12 +149,12 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
     // the loads of UA cells are issued before any of them is finished
     using AdjIn = std::conditional_t<MODE == XM_ADJ1, Adj1In, Adj2In>;
     constexpr int UA = 4;
-    for (int base = 0; base < TY * Q; base += UA * NT) {
+    for (int base = 0; base < TY * Q; base += UA * NTB) {
       AdjIn in[UA];
       bool ok[UA];
 #pragma unroll
       for (int u = 0; u < UA; ++u) {
-        const int idx = base + u * NT + tid;
+        const int idx = base + u * NTB + tid;
         const int t = idx / Q, x = idx - t * Q, y = y0 + t;
         ok[u] = idx < TY * Q && x < nx && y < ny;
         if (ok[u]) {
@@ -141,7 +165,7 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
       }
 #pragma unroll
       for (int u = 0; u < UA; ++u) {
-        const int idx = base + u * NT + tid;
+        const int idx = base + u * NTB + tid;
         if (idx >= TY * Q) continue;
         const int t = idx / Q, x = idx - t * Q, y = y0 + t;
         float* hp = hs + t * Q + x;
@@ -170,12 +194,12 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
     if (pairs) {
       constexpr int QP = Q / 2;
       constexpr int U2 = 2;
-      for (int base = 0; base < TY * QP; base += U2 * NT) {
+      for (int base = 0; base < TY * QP; base += U2 * NTB) {
         CellState ca[U2], cb[U2];
         bool ok[U2];
 #pragma unroll
         for (int u = 0; u < U2; ++u) {
-          const int idx = base + u * NT + tid;
+          const int idx = base + u * NTB + tid;
           const int t = idx / QP, x = 2 * (idx - t * QP), y = y0 + t;
           ok[u] = idx < TY * QP && x < nx && y < ny;
           if (ok[u]) {
@@ -186,7 +210,7 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
         }
 #pragma unroll
         for (int u = 0; u < U2; ++u) {
-          const int idx = base + u * NT + tid;
+          const int idx = base + u * NTB + tid;
           if (idx >= TY * QP) continue;
           const int t = idx / QP, x = 2 * (idx - t * QP), y = y0 + t;
           float3 ra = make_float3(0.f, 0.f, 0.f), rb = ra;
@@ -202,12 +226,12 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
       }
     } else {
     constexpr int U = 4;
-    for (int base = 0; base < TY * Q; base += U * NT) {
+    for (int base = 0; base < TY * Q; base += U * NTB) {
       CellState cs[U];
       bool ok[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = base + u * NT + tid;
+        const int idx = base + u * NTB + tid;
         const int t = idx / Q, x = idx - t * Q, y = y0 + t;
         ok[u] = idx < TY * Q && x < nx && y < ny;
         if (ok[u]) {
@@ -217,7 +241,7 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = base + u * NT + tid;
+        const int idx = base + u * NTB + tid;
         if (idx >= TY * Q) continue;
         const int t = idx / Q, x = idx - t * Q, y = y0 + t;
         float3 r = make_float3(0.f, 0.f, 0.f);
@@ -235,21 +259,27 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
   __syncthreads();
   {
     float2 v[3][8];
+    if (fft_thread) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float2* h2 = reinterpret_cast<const float2*>(hs + (c * TY + ty) * Q);
+      for (int c = 0; c < 3; ++c) {
+        const float2* h2 = reinterpret_cast<const float2*>(hs + (c * TY + ty) * Q);
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        v[c][s] = h2[j + s * T];
-        v[c][s + 4] = make_float2(0.f, 0.f);
+        for (int s = 0; s < 4; ++s) {
+          v[c][s] = h2[j + s * T];
+          v[c][s + 4] = make_float2(0.f, 0.f);
+        }
       }
     }
     __syncthreads();   // hs is read; the transform's exchanges overwrite it
-    fft_reg<Q, -1, true, 3>(v, j, lines, LS, lp.twb);
+    if (fft_thread) {
+      fft_reg<Q, -1, true, 3>(v, j, lines, LS, lp.twb);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int r = 0; r < 8; ++r) lines[c * LS + pad16(j + r * T)] = v[c][r];
+        for (int r = 0; r < 8; ++r) lines[c * LS + pad16(j + r * T)] = v[c][r];
+    } else {
+      fft_reg_barriers<Q>();
+    }
   }
   __syncthreads();
   // split and store, TY rows of S contiguous; one pass over k = 0..Q/2 gives both X_k and
@@ -257,7 +287,7 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
   // c = W^k b (W = exp(-2 pi i / 2Q), W^{Q-k} = -conj W^k):
   //   X_k = (a - i c)/2,  X_{Q-k} = (conj a - i conj c)/2   (k = 0 gives X_0 and X_Q)
   constexpr int QH = Q / 2 + 1;
-  for (int idx = tid; idx < 3 * QH * TY; idx += NT) {
+  for (int idx = tid; idx < 3 * QH * TY; idx += NTB) {
     const int t = idx % TY, r = idx / TY, k = r % QH, c = r / QH;
     const int yy = y0 + t;
     if (yy >= ny) continue;
@@ -271,17 +301,21 @@ __global__ void __launch_bounds__(TY * Q / 8 < 256 ? TY * Q / 8 : 256, TY * Q / 
   }
 }
 
+template <int Q, int TY, int MODE>
+cudaError_t launch_qtm(const FilmDev* films, const LaunchP& lp, int nunits, size_t smem, cudaStream_t s) {
+  return launch_pdl(kx_fast<Q, TY, MODE>, nunits, x_threads(Q, TY, MODE), smem, s, films, lp);
+}
+
 template <int Q, int TY>
 cudaError_t launch_qt(int mode, const FilmDev* films, const LaunchP& lp, int nunits, size_t smem, cudaStream_t s) {
-  const unsigned threads = TY * (Q / 8);
   switch (mode) {
-    case XM_R2C: return launch_pdl(kx_fast<Q, TY, XM_R2C>, nunits, threads, smem, s, films, lp);
-    case XM_HEFF: return launch_pdl(kx_fast<Q, TY, XM_HEFF>, nunits, threads, smem, s, films, lp);
-    case XM_ADJ1: return launch_pdl(kx_fast<Q, TY, XM_ADJ1>, nunits, threads, smem, s, films, lp);
-    case XM_ADJ2: return launch_pdl(kx_fast<Q, TY, XM_ADJ2>, nunits, threads, smem, s, films, lp);
-    case XM_HEUN1: return launch_pdl(kx_fast<Q, TY, XM_HEUN1>, nunits, threads, smem, s, films, lp);
-    case XM_HEUN2: return launch_pdl(kx_fast<Q, TY, XM_HEUN2>, nunits, threads, smem, s, films, lp);
-    default: return launch_pdl(kx_fast<Q, TY, XM_STEP>, nunits, threads, smem, s, films, lp);
+    case XM_R2C: return launch_qtm<Q, TY, XM_R2C>(films, lp, nunits, smem, s);
+    case XM_HEFF: return launch_qtm<Q, TY, XM_HEFF>(films, lp, nunits, smem, s);
+    case XM_ADJ1: return launch_qtm<Q, TY, XM_ADJ1>(films, lp, nunits, smem, s);
+    case XM_ADJ2: return launch_qtm<Q, TY, XM_ADJ2>(films, lp, nunits, smem, s);
+    case XM_HEUN1: return launch_qtm<Q, TY, XM_HEUN1>(films, lp, nunits, smem, s);
+    case XM_HEUN2: return launch_qtm<Q, TY, XM_HEUN2>(films, lp, nunits, smem, s);
+    default: return launch_qtm<Q, TY, XM_STEP>(films, lp, nunits, smem, s);
   }
 }
 

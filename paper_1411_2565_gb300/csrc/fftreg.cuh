@@ -153,6 +153,26 @@ __device__ __forceinline__ void fft_reg_stage(float2 (&v)[G][8], int j, float2* 
   }
 }
 
+// The barriers of fft_reg<L, ...> alone, for threads of the block that hold no line: the
+// same stage recursion, two __syncthreads() per exchange.  A block whose threads split
+// into transforming and non-transforming groups must split them by whole warps.
+template <int L, int NS>
+__device__ __forceinline__ void fft_reg_barriers_stage() {
+  constexpr int REM = L / NS;
+  constexpr int R = REM >= 8 ? 8 : REM;
+  constexpr bool LAST = (NS * R == L);
+  if constexpr (R == 8 && !LAST) {
+    __syncthreads();
+    __syncthreads();
+    fft_reg_barriers_stage<L, NS * 8>();
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void fft_reg_barriers() {
+  fft_reg_barriers_stage<L, 1>();
+}
+
 // In-place transform of G lines held by the calling thread (see the file comment);
 // tw is the per-base twiddle table (twb_at).
 template <int L, int DIR, bool ZU, int G>
