@@ -60,6 +60,7 @@ struct Group {
   bool fused = true;
   int Q = 0, Py = 0, nz = 0, Pz = 0;
   int TY = 1, KPB = 1, RPB = 1, TQ = 1;
+  bool xhelp = false;       // x pass with helper warps (few blocks in flight)
   int units[UK_COUNT] = {0, 0, 0, 0, 0};
   size_t smem_x = 0, smem_yz = 0, smem_y = 0, smem_z = 0;
   size_t o_desc = 0;
@@ -180,15 +181,21 @@ int plan_group(grace_ctx* c, Group& g) {
     return u;
   };
   const long long want = 2LL * sm_count();
+  // With fewer blocks than two per SM the x pass is latency-bound: take one line per block,
+  // or the large tile when only it fills whole warps and so can take helper warps.
   auto pick_x_tile = [&]() {
     const int big = fast_x_tile(g.Q);
     if (c->tile_x == 1) return 1;                 // explicit: one line per block
     if (c->tile_x > 1) return big;                // explicit: the large compiled tile
-    return (big > 1 && xunits(big) < want) ? 1 : big;
+    if (big > 1 && xunits(big) < want)
+      return (!fast_x_helper_tile(g.Q, 1) && fast_x_helper_tile(g.Q, big)) ? big : 1;
+    return big;
   };
+  auto pick_x_help = [&]() { return fast_x_helper_tile(g.Q, g.TY) && xunits(g.TY) < want; };
   if (g.split_fast) {
     g.fused = false;
     g.TY = pick_x_tile();
+    g.xhelp = pick_x_help();
     g.smem_x = fast_x_smem(g.Q, g.TY);
     g.RPB = fast_y_rows(g.Py);
     g.TQ = fast_z_cols(g.Pz);
@@ -196,6 +203,7 @@ int plan_group(grace_ctx* c, Group& g) {
   } else if (g.fast) {
     g.fused = true;
     g.TY = pick_x_tile();      // one of the two compile-time tiles of the fast x pass
+    g.xhelp = pick_x_help();
     g.smem_x = fast_x_smem(g.Q, g.TY);
     const int per = g.nz * (g.Py / 8);
     int KPB = c->tile_yz > 0 ? c->tile_yz : std::max(1, 128 / per);
@@ -463,6 +471,7 @@ LaunchP group_lp(const grace_ctx* c, const Group& g) {
   lp.twb = reinterpret_cast<const float2*>(c->ws + c->o_tw);
   lp.tw = lp.twb + (GRACE_LMAX - 2);   // the base-GRACE_LMAX table
   lp.pdl = c->pdl ? 1 : 0;
+  lp.xhelp = g.xhelp ? 1 : 0;
   lp.k1 = reinterpret_cast<float*>(c->ws + c->o_run + c->o_k1);
   lp.hscale = c->pulse ? time_scale(c) : nullptr;
   return lp;

@@ -37,6 +37,8 @@ bool fast_x_supported(int Q) { return Q >= 8 && Q <= 2048; }
 
 int fast_x_tile(int Q) { return fastx::x_tile(Q); }
 
+bool fast_x_helper_tile(int Q, int TY) { return fastx::x_helper_tile(Q, TY); }
+
 size_t fast_x_smem(int Q, int TY) {
   const size_t lines = (size_t)3 * TY * fastx::x_line_stride(Q, TY) * sizeof(float2);
   const size_t hs = (size_t)3 * TY * Q * sizeof(float);

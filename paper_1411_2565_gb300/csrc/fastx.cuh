@@ -36,30 +36,35 @@ __host__ __device__ constexpr int x_tile(int Q) {
   return (256 / (Q / 8)) < 1 ? 1 : ((256 / (Q / 8)) > 4 ? 4 : 256 / (Q / 8));
 }
 
-// Threads per block: TY Q/8 transform the lines.  The adjoint modes, whose per-cell work
-// dominates, add three helper threads per transforming thread when the transforming
-// threads fill one or two whole warps: the helpers share the staging, the cell update
-// and the split, and only keep step with the transforms' barriers.
-__host__ __device__ constexpr bool x_helpers(int Q, int TY, int MODE) {
-  return (MODE == XM_ADJ1 || MODE == XM_ADJ2) && (TY * Q / 8) % 32 == 0 && TY * Q / 8 <= 64;
+// Threads per block: TY Q/8 transform the lines.  When those fill one or two whole warps a
+// tile may add three helper threads per transforming thread: the helpers share the
+// staging, the cell update and the split, and only keep step with the transforms'
+// barriers.  The adjoint modes, whose per-cell work dominates, always take them; the
+// others when the launch has few blocks (H, chosen by the planner).
+__host__ __device__ constexpr bool x_helper_tile(int Q, int TY) {
+  return (TY * Q / 8) % 32 == 0 && TY * Q / 8 <= 64;
 }
-__host__ __device__ constexpr int x_threads(int Q, int TY, int MODE) {
-  return x_helpers(Q, TY, MODE) ? 4 * (TY * Q / 8) : TY * Q / 8;
+__host__ __device__ constexpr bool x_adjoint(int MODE) { return MODE == XM_ADJ1 || MODE == XM_ADJ2; }
+__host__ __device__ constexpr bool x_helpers(int Q, int TY, int MODE, bool H) {
+  return x_helper_tile(Q, TY) && (H || x_adjoint(MODE));
+}
+__host__ __device__ constexpr int x_threads(int Q, int TY, int MODE, bool H) {
+  return x_helpers(Q, TY, MODE, H) ? 4 * (TY * Q / 8) : TY * Q / 8;
 }
 // Resident blocks the register bound aims at: 128-thread tiles 6 (up to 80 registers;
 // measured faster than 4 despite a few spilled bytes), blocks with helpers 512 threads per
 // SM in all, others 2.
-__host__ __device__ constexpr int x_min_blocks(int Q, int TY, int MODE) {
-  return x_helpers(Q, TY, MODE) ? 512 / x_threads(Q, TY, MODE) : (TY * Q / 8 == 128 ? 6 : 2);
+__host__ __device__ constexpr int x_min_blocks(int Q, int TY, int MODE, bool H) {
+  return x_helpers(Q, TY, MODE, H) ? 512 / x_threads(Q, TY, MODE, H) : (TY * Q / 8 == 128 ? 6 : 2);
 }
 
-template <int Q, int TY, int MODE>
-__global__ void __launch_bounds__(x_threads(Q, TY, MODE) < 256 ? x_threads(Q, TY, MODE) : 256,
-                                  x_min_blocks(Q, TY, MODE))
+template <int Q, int TY, int MODE, bool H>
+__global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q, TY, MODE, H) : 256,
+                                  x_min_blocks(Q, TY, MODE, H))
     kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = Q / 8;
-  constexpr int NT = TY * T;                      // transforming threads
-  constexpr int NTB = x_threads(Q, TY, MODE);     // all threads of the block
+  constexpr int NT = TY * T;                         // transforming threads
+  constexpr int NTB = x_threads(Q, TY, MODE, H);     // all threads of the block
   constexpr int LS = x_line_stride(Q, TY);
   const int tid = threadIdx.x;
   const int j = tid % T, ty = tid / T;
@@ -303,7 +308,21 @@ __global__ void __launch_bounds__(x_threads(Q, TY, MODE) < 256 ? x_threads(Q, TY
 
 template <int Q, int TY, int MODE>
 cudaError_t launch_qtm(const FilmDev* films, const LaunchP& lp, int nunits, size_t smem, cudaStream_t s) {
-  return launch_pdl(kx_fast<Q, TY, MODE>, nunits, x_threads(Q, TY, MODE), smem, s, films, lp);
+  if constexpr (x_helper_tile(Q, TY) && !x_adjoint(MODE)) {
+    if (lp.xhelp)
+      return launch_pdl(kx_fast<Q, TY, MODE, true>, nunits, x_threads(Q, TY, MODE, true), smem, s, films, lp);
+  }
+  return launch_pdl(kx_fast<Q, TY, MODE, false>, nunits, x_threads(Q, TY, MODE, false), smem, s, films, lp);
+}
+
+template <int Q, int TY, int MODE>
+cudaError_t attr_qtm(size_t smem) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, MODE, false>, a, (int)smem);
+  if constexpr (x_helper_tile(Q, TY) && !x_adjoint(MODE)) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, MODE, true>, a, (int)smem);
+  }
+  return e;
 }
 
 template <int Q, int TY>
@@ -321,14 +340,13 @@ cudaError_t launch_qt(int mode, const FilmDev* films, const LaunchP& lp, int nun
 
 template <int Q, int TY>
 cudaError_t attr_qt(size_t smem) {
-  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_R2C>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_HEFF>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_STEP>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_ADJ1>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_ADJ2>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_HEUN1>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kx_fast<Q, TY, XM_HEUN2>, a, (int)smem);
+  cudaError_t e = attr_qtm<Q, TY, XM_R2C>(smem);
+  if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_HEFF>(smem);
+  if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_STEP>(smem);
+  if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_ADJ1>(smem);
+  if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_ADJ2>(smem);
+  if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_HEUN1>(smem);
+  if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_HEUN2>(smem);
   return e;
 }
 

@@ -70,6 +70,7 @@ struct LaunchP {
   const float2* tw;  // twiddle table exp(-2 pi i m / GRACE_LMAX), GRACE_LMAX entries
   const float2* twb; // per-base twiddle tables: exp(-2 pi i k / B) at twb[B - 2 + k], B = 2..GRACE_LMAX
   int pdl;          // launch with programmatic stream serialization
+  int xhelp;        // x pass: helper warps on one- and two-warp tiles (few blocks in flight)
   float* k1;        // Heun: f(m_n), concatenated films (3 N)
   const float* hscale;  // applied-field envelope {s(t_n), s(t_n + dt)}, nullptr: constant field
   // adjoint (concatenated films; nullptr when unused)
@@ -150,6 +151,7 @@ cudaError_t launch_energy(const FilmDev* films, const LaunchP& lp, const float* 
 // Fast kernels with compile-time FFT lengths (fastx.cu, fastyz.cu).
 bool fast_x_supported(int Q);
 int fast_x_tile(int Q);
+bool fast_x_helper_tile(int Q, int TY);   // the tile can take helper warps (LaunchP::xhelp)
 size_t fast_x_smem(int Q, int TY);
 cudaError_t configure_fast_x(int Q, int TY, size_t smem);
 cudaError_t launch_fast_x(int Q, int mode, const FilmDev* films, const LaunchP& lp, int nunits, int TY,
