@@ -51,8 +51,9 @@ constexpr int kEnergyBlocks = 304;
 
 }  // namespace
 
-// Films launched together: either one fast group per (Q, Py, nz) with compile-time FFT
-// lengths, or one generic group (runtime lengths) for everything else.
+// Films launched together: one fast group per (Q, Py, nz) (fused y-z pass, nz <= 4) or per
+// (Q, Py, Pz) (split y and z passes) with compile-time FFT lengths, and one generic group
+// (runtime lengths) for everything else.
 struct Group {
   std::vector<int> idx;
   bool fast = false;        // compile-time FFT lengths (fused y-z, or split when split_fast)
