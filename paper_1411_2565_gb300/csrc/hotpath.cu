@@ -39,13 +39,12 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
   const int local = unit - f.u0[UK_X];
   const int z = local / nyt;
   const int y0 = (local - z * nyt) * TY;
-  const int nx = f.nx, ny = f.ny, nz = f.nz, Q = f.Q;
+  const int nx = f.nx, ny = f.ny, Q = f.Q;
   const int lsx = line_stride(Q > 0 ? Q : 1);
   extern __shared__ float4 smem4[];
   float2* cb = reinterpret_cast<float2*>(smem4);
   float* rb = reinterpret_cast<float*>(cb + TY * lsx);     // [3][TY][nx]
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int N = f.ncell;
   const float* __restrict__ m = lp.mk ? lp.mk + 3 * f.cell0 : (lp.parity ? f.m1 : f.m0);
   const int twq = Q > 0 ? GRACE_LMAX / (2 * Q) : 0;      // table step for W^k, P = 2Q
 
@@ -124,7 +123,8 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
   }
   __syncthreads();
 
-  const bool r2c = (MODE != XM_HEFF && MODE != XM_ADJ2) || (MODE == XM_HEFF && demag);
+  if constexpr (MODE == XM_ADJ2) return;      // D(nu) feeds no forward transform
+  const bool r2c = MODE != XM_HEFF || demag;
   if (!r2c) return;
   for (int c = 0; c < 3; ++c) {
     if (Q == 0) {
