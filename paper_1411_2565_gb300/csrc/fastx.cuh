@@ -87,7 +87,6 @@ __global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q,
   const bool demag = (MODE == XM_STEP) || (MODE == XM_ADJ1) || (MODE == XM_ADJ2) ||
                      (MODE == XM_HEUN1) || (MODE == XM_HEUN2) ||
                      (MODE == XM_HEFF && (lp.mask & 1u));
-  const int nst = 3 * (Q + 1) * TY;
 
   pdl_launch_dependents();
   {
@@ -103,14 +102,36 @@ __global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q,
   pdl_wait();
 
   if (demag) {
-    // staging S -> shared, TY rows contiguous, as asynchronous copies: every load of the
-    // block is in flight at once and none holds a register
+    // staging S -> shared as asynchronous copies (every load of the block in flight at
+    // once, none holding a register) into st[c][k][t], over the line buffers: the TY rows
+    // of one (c, k) are adjacent in S, so two rows go in one 16-byte copy where the row
+    // length keeps 16-byte alignment and both rows exist
+    float2* st = sm;
+    if constexpr (TY >= 2) {
+      const bool wide = (srow & 1) == 0;
+      constexpr int TP = TY / 2;
 #pragma unroll 4
-    for (int idx = tid; idx < nst; idx += NTB) {
-      const int t = idx % TY, r = idx / TY, k = r % (Q + 1), c = r / (Q + 1);
-      float2* dst = sm + (3 * t + c) * LS + pad16(k);
-      if (y0 + t < ny) cp_async8(dst, Sz + c * sc + (size_t)k * srow + y0 + t);
-      else *dst = make_float2(0.f, 0.f);
+      for (int idx = tid; idx < 3 * (Q + 1) * TP; idx += NTB) {
+        const int t = 2 * (idx % TP), r = idx / TP;           // r = c (Q + 1) + k
+        const int k = r % (Q + 1), c = r / (Q + 1);
+        float2* dst = st + r * TY + t;
+        const float2* src = Sz + c * sc + (size_t)k * srow + y0 + t;
+        if (wide && y0 + t + 1 < ny) {
+          cp_async16(dst, src);
+        } else {
+          if (y0 + t < ny) cp_async8(dst, src);
+          else dst[0] = make_float2(0.f, 0.f);
+          if (y0 + t + 1 < ny) cp_async8(dst + 1, src + 1);
+          else dst[1] = make_float2(0.f, 0.f);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int idx = tid; idx < 3 * (Q + 1); idx += NTB) {
+        const int k = idx % (Q + 1), c = idx / (Q + 1);
+        if (y0 < ny) cp_async8(st + idx, Sz + c * sc + (size_t)k * srow + y0);
+        else st[idx] = make_float2(0.f, 0.f);
+      }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -123,7 +144,7 @@ __global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q,
         const float2 w = twb_at<+1>(lp.twb, 2 * Q, k);   // W^{-k}, P = 2Q
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float2 xk = lines[c * LS + pad16(k)], xq = lines[c * LS + pad16(Q - k)];
+          const float2 xk = st[(c * (Q + 1) + k) * TY + ty], xq = st[(c * (Q + 1) + Q - k) * TY + ty];
           const float2 a = cadd(xk, cconj(xq)), b = csub(xk, cconj(xq));
           const float2 wb = cmul(w, b);
           v[c][r] = make_float2(a.x - wb.y, a.y + wb.x);
@@ -291,18 +312,40 @@ __global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q,
   // X_{Q-k} from the same Z_k, Z_{Q-k}: with a = Z_k + conj Z_{Q-k}, b = Z_k - conj Z_{Q-k},
   // c = W^k b (W = exp(-2 pi i / 2Q), W^{Q-k} = -conj W^k):
   //   X_k = (a - i c)/2,  X_{Q-k} = (conj a - i conj c)/2   (k = 0 gives X_0 and X_Q)
+  // Two adjacent rows (t, t + 1) per thread where TY >= 2: their outputs for one k sit
+  // side by side in S and go out as one 16-byte store when the row length allows.
   constexpr int QH = Q / 2 + 1;
-  for (int idx = tid; idx < 3 * QH * TY; idx += NTB) {
-    const int t = idx % TY, r = idx / TY, k = r % QH, c = r / QH;
+  constexpr int TP = TY >= 2 ? 2 : 1;
+  const bool wide = TP == 2 && (srow & 1) == 0;
+  for (int idx = tid; idx < 3 * QH * (TY / TP); idx += NTB) {
+    const int t = TP * (idx % (TY / TP)), r = idx / (TY / TP), k = r % QH, c = r / QH;
     const int yy = y0 + t;
     if (yy >= ny) continue;
-    const float2* ln = sm + (3 * t + c) * LS;
-    const float2 zk = ln[pad16(k)], zq = ln[pad16((Q - k) & (Q - 1))];
-    const float2 a = cadd(zk, cconj(zq)), b = csub(zk, cconj(zq));
-    const float2 wb = cmul(twb_at<-1>(lp.twb, 2 * Q, k), b);
+    const float2 w = twb_at<-1>(lp.twb, 2 * Q, k);
+    float2 xk[TP], xq[TP];
+#pragma unroll
+    for (int u = 0; u < TP; ++u) {
+      const float2* ln = sm + (3 * (t + u) + c) * LS;
+      const float2 zk = ln[pad16(k)], zq = ln[pad16((Q - k) & (Q - 1))];
+      const float2 a = cadd(zk, cconj(zq)), b = csub(zk, cconj(zq));
+      const float2 wb = cmul(w, b);
+      xk[u] = make_float2(0.5f * (a.x + wb.y), 0.5f * (a.y - wb.x));
+      xq[u] = make_float2(0.5f * (a.x - wb.y), -0.5f * (a.y + wb.x));
+    }
     float2* dst = Sz + c * sc + yy;
-    dst[(size_t)k * srow] = make_float2(0.5f * (a.x + wb.y), 0.5f * (a.y - wb.x));
-    if (k != Q / 2) dst[(size_t)(Q - k) * srow] = make_float2(0.5f * (a.x - wb.y), -0.5f * (a.y + wb.x));
+    if (TP == 2 && wide && yy + 1 < ny) {
+      *reinterpret_cast<float4*>(dst + (size_t)k * srow) = make_float4(xk[0].x, xk[0].y, xk[TP - 1].x, xk[TP - 1].y);
+      if (k != Q / 2)
+        *reinterpret_cast<float4*>(dst + (size_t)(Q - k) * srow) =
+            make_float4(xq[0].x, xq[0].y, xq[TP - 1].x, xq[TP - 1].y);
+    } else {
+#pragma unroll
+      for (int u = 0; u < TP; ++u) {
+        if (yy + u >= ny) break;
+        dst[(size_t)k * srow + u] = xk[u];
+        if (k != Q / 2) dst[(size_t)(Q - k) * srow + u] = xq[u];
+      }
+    }
   }
 }
 
