@@ -97,6 +97,9 @@ struct grace_ctx {
   double pulse_t[3] = {0.0, 0.0, 0.0};
   int graph_steps = 16;
   cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> aux;    // one per group past the first: groups step side by side
+  std::vector<cudaEvent_t> aux_join;
+  cudaEvent_t aux_fork = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   double gdt[2] = {0.0, 0.0};
   bool trace = false;
@@ -536,34 +539,86 @@ cudaError_t enqueue_x(grace_ctx* c, const Group& g, int mode, const LaunchP& lp,
   return cudaSuccess;
 }
 
-// One time step from the state in buffer `parity`.  Euler leaves the new state in the other
-// buffer; Heun (predictor into the other buffer, corrector back into this one) leaves it in
-// the same buffer.
+// One time step of group g from the state in buffer `parity`.  Euler leaves the new
+// state in the other buffer; Heun (predictor into the other buffer, corrector back into
+// this one) leaves it in the same buffer.
+cudaError_t enqueue_group_step(grace_ctx* c, const Group& g, int parity, float dt, cudaStream_t s) {
+  LaunchP lp = group_lp(c, g);
+  lp.parity = parity;
+  lp.dt = dt;
+  cudaError_t e = enqueue_conv(c, g, lp, s);
+  if (e != cudaSuccess) return e;
+  if (c->integrator == 1) {
+    e = enqueue_x(c, g, XM_HEUN1, lp, s);
+    if (e != cudaSuccess) return e;
+    e = enqueue_conv(c, g, lp, s);
+    if (e != cudaSuccess) return e;
+    LaunchP lp2 = lp;
+    lp2.parity = parity ^ 1;
+    return enqueue_x(c, g, XM_HEUN2, lp2, s);
+  }
+  return enqueue_x(c, g, XM_STEP, lp, s);
+}
+
+// One time step of every group, on stream s.
 cudaError_t enqueue_step(grace_ctx* c, int parity, float dt, double ddt, cudaStream_t s) {
   if (c->pulse) {   // envelope at t_n and t_n + dt for this step, then t <- t + dt
     cudaError_t e = launch_field_time(dev_time(c), time_scale(c), ddt, true, c->pulse_t, s);
     if (e != cudaSuccess) return e;
   }
   for (const auto& g : c->groups) {
-    LaunchP lp = group_lp(c, g);
-    lp.parity = parity;
-    lp.dt = dt;
-    cudaError_t e = enqueue_conv(c, g, lp, s);
-    if (e != cudaSuccess) return e;
-    if (c->integrator == 1) {
-      e = enqueue_x(c, g, XM_HEUN1, lp, s);
-      if (e != cudaSuccess) return e;
-      e = enqueue_conv(c, g, lp, s);
-      if (e != cudaSuccess) return e;
-      LaunchP lp2 = lp;
-      lp2.parity = parity ^ 1;
-      e = enqueue_x(c, g, XM_HEUN2, lp2, s);
-    } else {
-      e = enqueue_x(c, g, XM_STEP, lp, s);
-    }
+    cudaError_t e = enqueue_group_step(c, g, parity, dt, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+int parity_flip(const grace_ctx* c);
+
+// n steps from the state in buffer `parity`.  Groups share nothing but the envelope, so
+// with several groups and no envelope each group takes its n steps on a stream of its
+// own (forked from s and joined back into it): small groups run beside large ones, and a
+// captured graph holds one branch per group.
+cudaError_t enqueue_steps(grace_ctx* c, int n, int parity, float dt, double ddt, cudaStream_t s) {
+  const int flip = parity_flip(c);
+  const size_t ng = c->groups.size();
+  if (ng < 2 || c->pulse) {
+    for (int k = 0; k < n; ++k) {
+      cudaError_t e = enqueue_step(c, (parity + k * flip) & 1, dt, ddt, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  if (!c->aux_fork) {
+    cudaError_t e = cudaEventCreateWithFlags(&c->aux_fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  while (c->aux.size() + 1 < ng) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      if (st) cudaStreamDestroy(st);
+      return e;
+    }
+    c->aux.push_back(st);
+    c->aux_join.push_back(ev);
+  }
+  cudaError_t e = cudaEventRecord(c->aux_fork, s);
+  for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+    cudaStream_t sg = gi == 0 ? s : c->aux[gi - 1];
+    if (gi > 0) e = cudaStreamWaitEvent(sg, c->aux_fork, 0);
+    for (int k = 0; k < n && e == cudaSuccess; ++k)
+      e = enqueue_group_step(c, c->groups[gi], (parity + k * flip) & 1, dt, sg);
+    if (gi > 0 && e == cudaSuccess) e = cudaEventRecord(c->aux_join[gi - 1], sg);
+  }
+  // join every branch that was forked, also after a failure, so that a capture can end
+  for (size_t gi = 1; gi < ng; ++gi) {
+    const cudaError_t e2 = cudaStreamWaitEvent(s, c->aux_join[gi - 1], 0);
+    if (e == cudaSuccess) e = e2;
+  }
+  return e;
 }
 
 int parity_flip(const grace_ctx* c) { return c->integrator == 1 ? 0 : 1; }
@@ -930,8 +985,7 @@ int grace_step(grace_ctx* c, int n, double dt) {
       // inside a graph plain serialisation measured faster than programmatic edges
       const bool pdl = c->pdl;
       c->pdl = false;
-      for (int s = 0; s < G && e == cudaSuccess; ++s)
-        e = enqueue_step(c, (p + s * parity_flip(c)) & 1, fdt, dt, c->cap);
+      e = enqueue_steps(c, G, p, fdt, dt, c->cap);
       c->pdl = pdl;
       cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
       if (e != cudaSuccess) {
@@ -949,9 +1003,9 @@ int grace_step(grace_ctx* c, int n, double dt) {
       done += G;
     }
   }
-  for (; done < n; ++done) {
-    GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, dt, c->stream));
-    c->parity ^= parity_flip(c);
+  if (done < n) {
+    GRACE_CUDA(c, enqueue_steps(c, n - done, c->parity, fdt, dt, c->stream));
+    c->parity = (c->parity + (n - done) * parity_flip(c)) & 1;
   }
   return GRACE_OK;
 }
@@ -1181,6 +1235,9 @@ int grace_destroy(grace_ctx* c) {
   if (!c) return GRACE_OK;
   drop_graphs(c);
   if (c->cap) cudaStreamDestroy(c->cap);
+  for (cudaStream_t st : c->aux) cudaStreamDestroy(st);
+  for (cudaEvent_t e : c->aux_join) cudaEventDestroy(e);
+  if (c->aux_fork) cudaEventDestroy(c->aux_fork);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   delete c;
   return GRACE_OK;
