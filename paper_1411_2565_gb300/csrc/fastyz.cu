@@ -121,26 +121,42 @@ __global__ void __launch_bounds__(256, 3) kyz_fast(const FilmDev* __restrict__ f
   // tensor product: ky and its mirror PY - ky share the tensor slots (parity sign only),
   // so one thread takes both and loads the slots once; the two unpaired rows, ky = 0 and
   // the Nyquist row PY/2, form one more task, so PY/2 tasks per column keep a 256-thread
-  // block to a single round
+  // block to a single round.  With few slots (nz <= 2) a thread loads the slots of UP
+  // tasks before computing any (small films give each thread several tasks).
   constexpr int NSLOT = NZ == 1 ? 4 : 6 * NZ - 2;
+  constexpr int UP = NSLOT <= 4 ? 4 : (NSLOT <= 10 ? 2 : 1);
   constexpr int KH2 = PY / 2;
   const int ntask = KPB * KH2;
-  for (int p = tid; p < ntask; p += blockDim.x) {
-    const int ki = p / KH2, kyp = p - ki * KH2;
-    const int kxx = kx0 + ki;
-    if (kxx >= f.Kx) continue;
-    const float* Tk = f.T + (size_t)kxx * f.nslot * f.Ky;
-    float2* row = sm + (size_t)ki * NL * LS;
-    float t[NSLOT];
+  for (int p0 = tid; p0 < ntask; p0 += UP * blockDim.x) {
+    float t[UP][NSLOT];
+    bool okp[UP];
 #pragma unroll
-    for (int s2 = 0; s2 < NSLOT; ++s2) t[s2] = __ldg(Tk + (size_t)s2 * f.Ky + kyp);
-    product_at<NZ, NSLOT>(row + pad16(kyp), LS, t, 1.f);
-    if (kyp > 0) {
-      product_at<NZ, NSLOT>(row + pad16(PY - kyp), LS, t, -1.f);
-    } else {
+    for (int u = 0; u < UP; ++u) {
+      const int p = p0 + u * blockDim.x;
+      const int ki = p / KH2, kyp = p - ki * KH2;
+      okp[u] = p < ntask && kx0 + ki < f.Kx;
+      if (okp[u]) {
+        const float* Tk = f.T + (size_t)(kx0 + ki) * f.nslot * f.Ky;
 #pragma unroll
-      for (int s2 = 0; s2 < NSLOT; ++s2) t[s2] = __ldg(Tk + (size_t)s2 * f.Ky + PY / 2);
-      product_at<NZ, NSLOT>(row + pad16(PY / 2), LS, t, 1.f);
+        for (int s2 = 0; s2 < NSLOT; ++s2) t[u][s2] = __ldg(Tk + (size_t)s2 * f.Ky + kyp);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UP; ++u) {
+      if (!okp[u]) continue;
+      const int p = p0 + u * blockDim.x;
+      const int ki = p / KH2, kyp = p - ki * KH2;
+      float2* row = sm + (size_t)ki * NL * LS;
+      product_at<NZ, NSLOT>(row + pad16(kyp), LS, t[u], 1.f);
+      if (kyp > 0) {
+        product_at<NZ, NSLOT>(row + pad16(PY - kyp), LS, t[u], -1.f);
+      } else {
+        const float* Tk = f.T + (size_t)(kx0 + ki) * f.nslot * f.Ky;
+        float tn[NSLOT];
+#pragma unroll
+        for (int s2 = 0; s2 < NSLOT; ++s2) tn[s2] = __ldg(Tk + (size_t)s2 * f.Ky + PY / 2);
+        product_at<NZ, NSLOT>(row + pad16(PY / 2), LS, tn, 1.f);
+      }
     }
   }
   __syncthreads();
