@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "LLG cell-steps/s on 1 GB300 (full H_eff + step), % HBM roofline, vs oracle"
 UNIT = "cell-steps/s"
 L2_FLUSH_BYTES = 256 << 20
+E2E_HANDLES = 4           # handles (and streams) taking the end-to-end steps in turn
 
 
 def parse():
@@ -288,17 +289,17 @@ def run_grace(args, rank, world, local):
 
     # end to end through the C ABI with host buffers: every step copies its input m from
     # page-locked host memory (grace_set_m_host), takes one step and copies the result back
-    # (grace_get_m_host_async).  The steps are independent, so two handles on two streams
-    # take alternate steps: one's copies overlap the other's kernels; a handle waits for
-    # its previous result before it starts its next step.
+    # (grace_get_m_host_async).  The steps are independent, so E2E_HANDLES handles on as many
+    # streams take the steps in turn: one's copies and kernels overlap the others'; a handle
+    # waits for its previous result before it starts its next step.
     g.close()
-    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(E2E_HANDLES)]
     ctxs = [Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=dev, stream=st) for st in streams]
     for c in ctxs:
         c.set_hext(f.hext)
-    host_in = [torch.from_numpy(m0.reshape(-1).copy()).pin_memory() for _ in range(2)]
-    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(2)]
-    for k in range(2):                     # untimed: one pass through each handle
+    host_in = [torch.from_numpy(m0.reshape(-1).copy()).pin_memory() for _ in range(E2E_HANDLES)]
+    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(E2E_HANDLES)]
+    for k in range(E2E_HANDLES):           # untimed: one pass through each handle
         ctxs[k].set_m_host(host_in[k].numpy())
         ctxs[k].step(1, w.dt)
         ctxs[k].get_m_host(host_out[k].numpy(), wait=False)
@@ -306,7 +307,7 @@ def run_grace(args, rank, world, local):
     barrier()
     t0 = time.perf_counter()
     for k in range(args.e2e_steps):
-        i = k & 1
+        i = k % E2E_HANDLES
         streams[i].synchronize()           # the handle's previous result has arrived
         ctxs[i].set_m_host(host_in[i].numpy())
         ctxs[i].step(1, w.dt)
@@ -316,10 +317,10 @@ def run_grace(args, rank, world, local):
     t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e = {"value": whole_job_rate(ncell, world, args.e2e_steps, t_e2e), "unit": UNIT,
            "h2d_bytes_per_step": 12 * ncell, "d2h_bytes_per_step": 12 * ncell,
-           "steps": args.e2e_steps,
-           "path": "grace_set_m_host + grace_step(1) + grace_get_m_host_async per step, two handles on "
-                   "two streams taking alternate steps (host wall clock, all copies inside)"}
-    e2e["results_identical_across_handles"] = bool(torch.equal(host_out[0], host_out[1]))
+           "steps": args.e2e_steps, "handles": E2E_HANDLES,
+           "path": "grace_set_m_host + grace_step(1) + grace_get_m_host_async per step, handles on "
+                   "separate streams taking the steps in turn (host wall clock, all copies inside)"}
+    e2e["results_identical_across_handles"] = bool(all(torch.equal(host_out[0], o) for o in host_out[1:]))
     for c in ctxs:
         c.close()
 
