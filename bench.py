@@ -201,6 +201,30 @@ def algorithmic_bytes(g, film):
             "per_cell": (4 * spec + tensor + 24 * N) / N}
 
 
+def five_pass_bytes(film):
+    """Bytes per step of a design that keeps every intermediate spectrum in HBM: x R2C
+    (12N in, 24 A1 out), y FFT (24 A1 in, 24 A2 out), z FFT + product + inverse z (24 A2 in,
+    T, 24 A2 out), inverse y (24 A2 in, 24 A1 out), x C2R + step (24 A1 + 12N in, 12N out);
+    for nz = 1 the y pass takes the product (T) and there is no z pass.  A1 = Kx ny nz and
+    A2 = Kx Py nz complex points, T the tensor octant (6 or 4 components)."""
+    nx, ny, nz = film.grid
+    def pad(n):
+        p = 1
+        while p < 2 * n - 1:
+            p *= 2
+        return p
+    Px, Py, Pz = pad(nx), pad(ny), pad(nz)
+    Kx, Ky, Kz = Px // 2 + 1, Py // 2 + 1, Pz // 2 + 1
+    N = nx * ny * nz
+    A1, A2 = Kx * ny * nz, Kx * Py * nz
+    if nz == 1:
+        T = Kx * Ky * 4 * 4
+        return 12 * N + 24 * A1 + 24 * A1 + T + 24 * A1 + 24 * A1 + 12 * N + 12 * N
+    T = Kx * Ky * Kz * 6 * 4
+    return (12 * N + 24 * A1 + 24 * A1 + 24 * A2 + 24 * A2 + T + 24 * A2 + 24 * A2 + 24 * A1 + 24 * A1
+            + 12 * N + 12 * N)
+
+
 def run_grace(args, rank, world, local):
     import numpy as np
     import torch
@@ -259,6 +283,12 @@ def run_grace(args, rank, world, local):
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     ncell = f.ncells
     value = whole_job_rate(ncell, world, args.steps, total_ms * 1e-3)
+    # the timed loop in five equal chunks: their rates' median, min and max
+    chunk = max(1, args.steps // 5)
+    rates = sorted(ncell * chunk / (sum(step_ms[i * chunk:(i + 1) * chunk]) * 1e-3) for i in range(5)
+                   if len(step_ms) >= (i + 1) * chunk)
+    runs = {"chunks": len(rates), "steps_per_chunk": chunk, "median": rates[len(rates) // 2],
+            "min": rates[0], "max": rates[-1]} if rates else None
 
     # per-kernel durations: the same flushed single steps again, with an event pair around
     # every kernel (the events separate the kernels, so this pass is not the headline)
@@ -273,6 +303,16 @@ def run_grace(args, rank, world, local):
     # dominant kernel and its roofline
     peak, peak_kind = measured_peaks()
     byt = algorithmic_bytes(g, f)
+    # the whole step against the HBM peak: the bytes this design moves (x pass + fused y-z
+    # pass, each array read and written once) and, for comparison, the five-pass model
+    # (x, y, z FFT passes with every intermediate spectrum in HBM)
+    step_s = total_ms * 1e-3 / args.steps
+    fused_b = byt["per_cell"] * ncell
+    model_b = five_pass_bytes(f)
+    step_roof = {"unit": "GB/s", "peak": peak, "peak_source": peak_kind, "step_us": round(step_s * 1e6, 2),
+                 "bytes_fused": int(fused_b), "frac_fused": round(fused_b / step_s / 1e9 / peak, 4),
+                 "bytes_five_pass_model": int(model_b),
+                 "frac_five_pass_model": round(model_b / step_s / 1e9 / peak, 4)}
     dom = max(trace.items(), key=lambda kv: kv[1][0])[0] if trace else None
     roof = None
     if dom in byt:
@@ -339,7 +379,8 @@ def run_grace(args, rank, world, local):
                    "padded": [int(2 ** math.ceil(math.log2(max(1, 2 * n - 1)))) for n in f.grid],
                    "initial_state": w.note, "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}", "wall_s_timed_loop": round(wall, 3)},
-        "roofline": roof, "kernels": kernels, "gpu_launches": launches, "e2e": e2e,
+        "roofline": roof, "step_roofline": step_roof, "runs_of_5": runs,
+        "kernels": kernels, "gpu_launches": launches, "e2e": e2e,
         "cpu_baseline": cpu, "clocks": clk, "workloads": extras,
     }
     if rank == 0:
