@@ -18,10 +18,11 @@
  *   - A batch of films concatenates the per-film arrays in film order.
  *   - "dev_" pointers are CUDA device pointers; "host_" pointers are host memory;
  *     double[3] arguments are host memory.
- *   - Ownership: the library owns only the opaque host handle.  It never allocates
- *     device memory: the caller supplies one workspace (grace_bind) and every I/O
- *     buffer, keeps them alive until grace_destroy (or until the pointer is replaced),
- *     and supplies the CUDA stream all work is queued on.
+ *   - Ownership: the library owns only the opaque host handle and the CUDA streams,
+ *     events and graphs it creates for itself (graph capture, side-by-side groups of a
+ *     batch).  It never allocates device memory: the caller supplies one workspace
+ *     (grace_bind) and every I/O buffer, keeps them alive until grace_destroy (or until
+ *     the pointer is replaced), and supplies the CUDA stream all work is ordered on.
  *   - Errors: every call returns a grace_status; no exception or abort crosses the
  *     ABI.  grace_last_error() describes the last failure of that handle.  Work is
  *     asynchronous on the bound stream; a kernel fault surfaces as GRACE_ECUDA at the
@@ -103,10 +104,12 @@ int grace_create(grace_ctx **out, const int grid[3], const double cell_m[3], dou
                  double A, double Ku, double alpha, double gamma0);
 
 /*
- * grace_batch_create - plan nfilms independent films stepped together (one grouped launch
- * per kernel for the whole ensemble).  Arrays hold nfilms entries (grid and cell_m: 3 per
- * film, row-major).  Films with the same (grid, cell) share one demag tensor.
- * Same validation as grace_create for every film; nfilms in 1..65536.
+ * grace_batch_create - plan nfilms independent films stepped together: films are grouped
+ * by padded shape, each group takes one launch per kernel and step, and during
+ * grace_step (without a time envelope) the groups run side by side on streams of their
+ * own, forked from and joined back into the bound stream.  Arrays hold nfilms entries
+ * (grid and cell_m: 3 per film, row-major).  Films with the same (grid, cell) share one
+ * demag tensor.  Same validation as grace_create for every film; nfilms in 1..65536.
  */
 int grace_batch_create(grace_ctx **out, int nfilms, const int *grid, const double *cell_m,
                        const double *Ms, const double *A, const double *Ku,
@@ -176,7 +179,10 @@ int grace_get_time(const grace_ctx *ctx, double *t_s);
 int grace_heff(grace_ctx *ctx, float *dev_h, unsigned term_mask);
 
 /* grace_step - n time steps of Eq. 3 with renormalisation, time step dt_s: explicit Euler,
- * or Heun when GRACE_OPT_INTEGRATOR is 1. */
+ * or Heun when GRACE_OPT_INTEGRATOR is 1.  Two launches per step (four on the split path
+ * of films thicker than four cells; twice that for Heun), replayed from captured CUDA
+ * graphs of GRACE_OPT_GRAPH_STEPS steps where n allows; asynchronous on the bound
+ * stream.  Advances the handle's time by n dt_s. */
 int grace_step(grace_ctx *ctx, int n, double dt_s);
 
 /*
@@ -194,7 +200,9 @@ int grace_energy(grace_ctx *ctx, double out[5], double mavg[3]);
  * Accumulates (adds into) dev_dL_dhext (3*N, gradient w.r.t. a per-cell applied field)
  * and dev_dL_dms (N, gradient w.r.t. a per-cell Ms) when non-NULL, and writes dL/dm_0
  * to dev_dL_dm0 when non-NULL.  The state is left at m_0.  Needs
- * grace_backward_workspace_size() bytes in dev_scratch.
+ * grace_backward_workspace_size() bytes in dev_scratch.  Built for the explicit Euler
+ * step and a constant applied field: with GRACE_OPT_INTEGRATOR = 1 or a time envelope
+ * set it returns GRACE_EUNSUPPORTED.
  */
 int grace_backward_workspace_size(const grace_ctx *ctx, int n, int ckpt_every, size_t *bytes);
 int grace_backward(grace_ctx *ctx, const float *dev_dL_dmT, int n, double dt_s, int ckpt_every,
@@ -204,8 +212,8 @@ int grace_backward(grace_ctx *ctx, const float *dev_dL_dmT, int n, double dt_s, 
 /*
  * grace_trace - capacity > 0 turns per-kernel timing on: the next `capacity` kernels
  * launched by grace_step / grace_heff / grace_set_m are bracketed by CUDA events on the
- * bound stream (events are created here, not during the timed work; later launches are
- * not timed) and grace_step uses plain launches instead of graphs.  0 turns it off.
+ * stream each is launched on (events are created here, not during the timed work; later
+ * launches are not timed) and grace_step uses plain launches instead of graphs.  0 turns it off.
  * grace_trace_read synchronises on the last event and returns, per GRACE_KERNEL_* kind,
  * the summed device time in ms and the number of timed launches since the previous
  * read (8 entries each); it then resets them and the capacity.
