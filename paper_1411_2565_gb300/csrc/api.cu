@@ -1212,7 +1212,8 @@ int grace_trace(grace_ctx* c, int capacity) {
 
 int grace_trace_read(grace_ctx* c, double ms[8], long long counts[8]) {
   if (!c || !ms || !counts) return GRACE_EINVAL;
-  if (c->ev_next > 0) GRACE_CUDA(c, cudaEventSynchronize(c->ev[c->ev_next - 1]));
+  // the pairs may sit on several streams (groups of a batch step side by side)
+  for (size_t i = 0; i + 1 < c->ev_next; i += 2) GRACE_CUDA(c, cudaEventSynchronize(c->ev[i + 1]));
   for (size_t i = 0; i + 1 < c->ev_next; i += 2) {
     float t = 0.f;
     GRACE_CUDA(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));

@@ -310,3 +310,31 @@ def test_async_host_copies_on_two_streams():
         s.synchronize()
     for o in outs:
         assert np.array_equal(o.numpy(), expect)
+
+
+def test_trace_counts_every_kernel_launch():
+    """grace_trace / grace_trace_read: one timed launch per kernel and group per step, also
+    when the groups of a batch run on streams of their own; the traced run computes the
+    same state as the graph run."""
+    Grace, GraceBatch = _grace()
+    f, m0 = workloads.small_film((64, 32, 2), seed=91)
+    a, b = make(f, m0), make(f, m0)
+    a.trace(1000)
+    a.step(5, 1e-14)
+    tr = a.trace_read()
+    assert {k: v[1] for k, v in tr.items()} == {"yz_fast": 5, "x_fast": 5}
+    assert all(v[0] > 0 for v in tr.values())
+    b.step(5, 1e-14)
+    assert torch.equal(a.get_m(), b.get_m())
+    # a batch of three size classes (three groups, three streams)
+    films = [workloads.small_film(g, seed=92 + k)[0] for k, g in enumerate([(64, 16, 1), (128, 32, 1), (64, 32, 2)])]
+    m0s = [workloads.small_film(fi.grid, seed=92 + k)[1] for k, fi in enumerate(films)]
+    gb = GraceBatch(films, device=DEV)
+    gb.set_m(torch.from_numpy(np.concatenate([m.reshape(-1) for m in m0s])).to(DEV))
+    gb.trace(1000)
+    gb.step(4, 1e-14)
+    tr = gb.trace_read()
+    assert sum(v[1] for v in tr.values()) == 2 * 3 * 4
+    gb.trace(0)
+    gb.step(16, 1e-14)                     # graphs with one branch per group
+    assert np.isfinite(gb.energy()[1]).all()
