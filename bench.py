@@ -469,7 +469,38 @@ def extra_workloads(dev):
                                 "(re-computes the forward inside)"}
     del g
     out["cufft_demag_comparison"] = cufft_demag_comparison(dev, flush)
+    out["cube_sweep"] = cube_sweep(dev)
     return out
+
+
+# the paper's Table 1: per-step time of its GPU code (HD 7970) for N^3 cubes, context only
+PAPER_TABLE1_GPU_MS = {8: 1.95, 16: 2.723, 32: 3.151, 64: 6.558, 128: 26.34}
+
+
+def cube_sweep(dev, steps=64):
+    """N^3 cubes of 1 nm cells in the paper's Table 1 material (A = 1e-11 J/m, Ms = 1e6 A/m,
+    H_anis = 100 kA/m along x, so Ku = mu0 Ms H_anis / 2), random unit m, dt = 1e-14 s:
+    cell-steps/s in graphs of 16 steps (working sets up to ~0.4 GB, L2 not flushed), next
+    to the paper's own per-step times (other hardware, context only)."""
+    import math
+    import torch
+
+    import workloads
+    from paper_1411_2565_gb300.grace import Grace
+    Ms, A, HK = 1e6, 1e-11, 1e5
+    Ku = 4e-7 * math.pi * Ms * HK / 2
+    res = {}
+    for n in sorted(PAPER_TABLE1_GPU_MS):
+        g = Grace((n, n, n), (1e-9, 1e-9, 1e-9), Ms, A, Ku, 0.1, device=dev)
+        g.set_m(torch.from_numpy(workloads.random_unit_m((n, n, n), seed=40 + n).reshape(-1)).to(dev))
+        g.step(32, 1e-14)
+        t = time_events(lambda: g.step(steps, 1e-14), 1)
+        g.close()
+        ms = t / steps * 1e3
+        res[f"{n}^3"] = {"cells": n ** 3, "ms_per_step": round(ms, 4), "value": n ** 3 / (ms * 1e-3),
+                         "paper_gpu_ms_per_step": PAPER_TABLE1_GPU_MS[n],
+                         "ratio_to_paper": round(PAPER_TABLE1_GPU_MS[n] / ms, 1)}
+    return res
 
 
 def cufft_demag_comparison(dev, flush, reps=20):
