@@ -84,26 +84,15 @@ __device__ __forceinline__ CellState cell_field(const FilmDev& f, unsigned mask,
   return c;
 }
 
-// One row of m around a cell pair: p[k * stride] is component k at the pair's x (p may
-// point into shared or global memory); p == nullptr: no such row (free boundary).
-struct RowRef {
-  const float* p;
-  int stride;
-};
-
 // cell_field for the two cells x, x + 1 of a row (x even, nx even, the film's arrays
 // 8-byte aligned): the pair's centres and y / z neighbours come in 8-byte loads and the
-// two share their x neighbours.  The arithmetic is cell_field's, term for term.  The
-// rows come as RowRefs: the pair's own row (its x neighbours are read there too), the
-// rows y - 1 / y + 1 and the rows in the planes z - 1 / z + 1; i is the global index of
-// cell x (per-cell Ms and field).
-__device__ __forceinline__ void cell_field_pair_rows(const FilmDev& f, unsigned mask, RowRef ctr, RowRef ylo,
-                                                     RowRef yhi, RowRef zlo, RowRef zhi, int i, int x,
-                                                     float2 hdx, float2 hdy, float2 hdz, float hs, CellState& ca,
-                                                     CellState& cb) {
-  const int N = f.ncell, nx = f.nx;
-  auto ld2 = [](RowRef r, int k) { return *reinterpret_cast<const float2*>(r.p + k * r.stride); };
-  const float2 mx = ld2(ctr, 0), my = ld2(ctr, 1), mz = ld2(ctr, 2);
+// two share their x neighbours.  The arithmetic is cell_field's, term for term.
+__device__ __forceinline__ void cell_field_pair(const FilmDev& f, unsigned mask, const float* __restrict__ m,
+                                                int i, int x, int y, int z, float2 hdx, float2 hdy,
+                                                float2 hdz, float hs, CellState& ca, CellState& cb) {
+  const int N = f.ncell, nx = f.nx, ny = f.ny, nz = f.nz;
+  auto ld2 = [&](int k) { return *reinterpret_cast<const float2*>(m + k); };
+  const float2 mx = ld2(i), my = ld2(N + i), mz = ld2(2 * N + i);
   ca.mx = mx.x; ca.my = my.x; ca.mz = mz.x;
   cb.mx = mx.y; cb.my = my.y; cb.mz = mz.y;
   if (f.ms_field) {
@@ -116,33 +105,31 @@ __device__ __forceinline__ void cell_field_pair_rows(const FilmDev& f, unsigned 
   float ax = hdx.x, ay = hdy.x, az = hdz.x, bx = hdx.y, by = hdy.y, bz = hdz.y;
   if (mask & 2u) {
     // x: cell a has (x - 1 if any) and b; cell b has a and (x + 2 if any)
-    const float* c0 = ctr.p;
-    const int cs = ctr.stride;
     float pax = 0.f, pay = 0.f, paz = 0.f, pbx = 0.f, pby = 0.f, pbz = 0.f;
-    if (x > 0) { pax += c0[-1] - mx.x; pay += c0[cs - 1] - my.x; paz += c0[2 * cs - 1] - mz.x; }
+    if (x > 0) { pax += m[i - 1] - mx.x; pay += m[N + i - 1] - my.x; paz += m[2 * N + i - 1] - mz.x; }
     pax += mx.y - mx.x; pay += my.y - my.x; paz += mz.y - mz.x;
     pbx += mx.x - mx.y; pby += my.x - my.y; pbz += mz.x - mz.y;
-    if (x + 2 < nx) { pbx += c0[2] - mx.y; pby += c0[cs + 2] - my.y; pbz += c0[2 * cs + 2] - mz.y; }
+    if (x + 2 < nx) { pbx += m[i + 2] - mx.y; pby += m[N + i + 2] - my.y; pbz += m[2 * N + i + 2] - mz.y; }
     float sax = pax * f.idx2, say = pay * f.idx2, saz = paz * f.idx2;
     float sbx = pbx * f.idx2, sby = pby * f.idx2, sbz = pbz * f.idx2;
     // y and z: both cells' neighbours in one 8-byte load per component
-    auto axis = [&](RowRef lo, RowRef hi, float id2) {
+    auto axis = [&](bool lo, bool hi, int step, float id2) {
       float qax = 0.f, qay = 0.f, qaz = 0.f, qbx = 0.f, qby = 0.f, qbz = 0.f;
-      if (lo.p) {
-        const float2 nxv = ld2(lo, 0), nyv = ld2(lo, 1), nzv = ld2(lo, 2);
+      if (lo) {
+        const float2 nxv = ld2(i - step), nyv = ld2(N + i - step), nzv = ld2(2 * N + i - step);
         qax += nxv.x - mx.x; qay += nyv.x - my.x; qaz += nzv.x - mz.x;
         qbx += nxv.y - mx.y; qby += nyv.y - my.y; qbz += nzv.y - mz.y;
       }
-      if (hi.p) {
-        const float2 nxv = ld2(hi, 0), nyv = ld2(hi, 1), nzv = ld2(hi, 2);
+      if (hi) {
+        const float2 nxv = ld2(i + step), nyv = ld2(N + i + step), nzv = ld2(2 * N + i + step);
         qax += nxv.x - mx.x; qay += nyv.x - my.x; qaz += nzv.x - mz.x;
         qbx += nxv.y - mx.y; qby += nyv.y - my.y; qbz += nzv.y - mz.y;
       }
       sax = fmaf(qax, id2, sax); say = fmaf(qay, id2, say); saz = fmaf(qaz, id2, saz);
       sbx = fmaf(qbx, id2, sbx); sby = fmaf(qby, id2, sby); sbz = fmaf(qbz, id2, sbz);
     };
-    axis(ylo, yhi, f.idy2);
-    axis(zlo, zhi, f.idz2);
+    axis(y > 0, y < ny - 1, nx, f.idy2);
+    axis(z > 0, z < nz - 1, nx * ny, f.idz2);
     const float cea = f.ms_field ? f.cex * __frcp_rn(ca.Ms) : f.cex_ms;
     const float ceb = f.ms_field ? f.cex * __frcp_rn(cb.Ms) : f.cex_ms;
     ax = fmaf(cea, sax, ax); ay = fmaf(cea, say, ay); az = fmaf(cea, saz, az);
@@ -166,17 +153,6 @@ __device__ __forceinline__ void cell_field_pair_rows(const FilmDev& f, unsigned 
   }
   ca.hx = ax; ca.hy = ay; ca.hz = az;
   cb.hx = bx; cb.hy = by; cb.hz = bz;
-}
-
-// cell_field_pair_rows with every row read from the film's global m.
-__device__ __forceinline__ void cell_field_pair(const FilmDev& f, unsigned mask, const float* __restrict__ m,
-                                                int i, int x, int y, int z, float2 hdx, float2 hdy,
-                                                float2 hdz, float hs, CellState& ca, CellState& cb) {
-  const int N = f.ncell, nx = f.nx, pl = f.nx * f.ny;
-  const RowRef none{nullptr, 0};
-  cell_field_pair_rows(f, mask, RowRef{m + i, N}, y > 0 ? RowRef{m + i - nx, N} : none,
-                       y < f.ny - 1 ? RowRef{m + i + nx, N} : none, z > 0 ? RowRef{m + i - pl, N} : none,
-                       z < f.nz - 1 ? RowRef{m + i + pl, N} : none, i, x, hdx, hdy, hdz, hs, ca, cb);
 }
 
 __device__ __forceinline__ float3 cross3(float ax, float ay, float az, float bx, float by, float bz) {
