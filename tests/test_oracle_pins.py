@@ -23,6 +23,8 @@ import os
 import numpy as np
 import pytest
 
+import workloads
+
 from oracle import adjoint as adj
 from oracle import demag as dm
 from oracle import llg
@@ -469,3 +471,23 @@ def test_adjoint_matches_central_differences():
     e = 1e-6
     fd = (L(m0_=m0 + e * v) - L(m0_=m0 - e * v)) / (2 * e)
     assert fd == pytest.approx(float((g_m0 * v).sum()), rel=1e-6)
+
+
+def test_adjoint_step_dot_product():
+    """<J v, w> = <v, J^T w> for one step m' = normalise(m + dt f(m, H(m))) with every term
+    on (per-cell Ms, anisotropy, per-cell field): J v by central differences of the FP64
+    step, J^T w from the oracle's adjoint step, for random directions v and w."""
+    grid, cell = (6, 4, 2), (4e-9, 4e-9, 3e-9)
+    m = _rand_m((2, 4, 6), 21)
+    Ms = 6e5 + 4e5 * workloads.uniform(22, 48).reshape(2, 4, 6)
+    hx = 2e4 * (2 * workloads.uniform(23, 144).reshape(3, 2, 4, 6) - 1)
+    p = llg.Params(cell, Ms, 1.3e-11, 3e4, 0.15, hext=hx)
+    D = llg.Demag(grid, cell)
+    dt = 3e-14
+    v = workloads.gaussian(24, 144).reshape(3, 2, 4, 6)
+    w = workloads.gaussian(25, 144).reshape(3, 2, 4, 6)
+    e = 1e-6
+    jv = (llg.euler_step(m + e * v, p, dt, D) - llg.euler_step(m - e * v, p, dt, D)) / (2 * e)
+    jtw, _, _ = adj.adjoint_step(m, w, p, dt, D)
+    lhs, rhs = float((jv * w).sum()), float((v * jtw).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-8)
