@@ -357,3 +357,37 @@ def test_degenerate_materials_and_calls(grid):
     m1 = g.get_m().cpu().numpy().reshape(m0.shape)
     ref = llg.euler_step(m0, params(f), 1e-14)
     assert np.abs(m1 - ref).max() <= 2e-6
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN injected into the state (host-side fault injection) propagates through a step
+    and grace_energy reports GRACE_ENONFINITE instead of returning numbers."""
+    f, m0 = workloads.small_film((16, 8, 2), seed=96)
+    bad = m0.copy()
+    bad[0, 1, 3, 5] = np.nan
+    g = make(f, bad)
+    g.step(2, 1e-14)
+    with pytest.raises(_lib.GraceError) as ei:
+        g.energy()
+    assert _lib.STATUS[ei.value.code] == "GRACE_ENONFINITE"
+
+
+def test_checkpoint_and_resume_in_a_new_handle():
+    """get_m / set_m (with the handle's time) as checkpoint and resume: 10 + 22 steps in two
+    handles equal 32 steps in one, bit for bit, also through a time envelope."""
+    f, m0 = workloads.small_film((40, 20, 2), seed=97, alpha=0.2, hext=(3e4, 0.0, 0.0))
+    pulse = (5e-14, 2e-13, 3e-13)
+    whole = make(f, m0)
+    whole.set_hext_pulse(pulse)
+    whole.step(32, 1e-14)
+    first = make(f, m0)
+    first.set_hext_pulse(pulse)
+    first.step(10, 1e-14)
+    ckpt, t = first.get_m().clone(), first.time
+    second = make(f, m0)
+    second.set_hext_pulse(pulse)
+    second.time = t
+    second.set_m(ckpt)
+    second.step(22, 1e-14)
+    assert torch.equal(second.get_m(), whole.get_m())
+    assert second.time == whole.time
