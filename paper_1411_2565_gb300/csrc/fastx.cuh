@@ -1,13 +1,16 @@
 // Fused x pass for films whose x transform has compile-time length Q = Px/2 >= 8.
 //
 // Block = TY consecutive y lines of one z plane, Q/8 threads per line (thread (ty, j),
-// ty fastest so that TY neighbouring rows of S are read and written together).
-// Per field component the x C2R runs in registers: thread j ends holding
-// y[j + s Q/8] = H(2n) + i H(2n+1), n = j + s Q/8, i.e. H at cells x = 2n, 2n+1 for
-// s < 4.  Those are exactly the cells whose new magnetisation forms its input
-// z[j + s Q/8] = M(2n) + i M(2n+1) to the forward transform, so C2R -> H_eff ->
-// Euler step (Eq. 3, renormalised) -> R2C never leaves registers; shared memory only
-// stages the spectrum for the Hermitian merge/split and carries the FFT exchanges.
+// j fastest), each transforming the 3 field components of its line (3 x 8 points in
+// registers).  Per block:
+//   1. the TY rows of S for every k are staged into shared memory with cp.async;
+//   2. Hermitian merge and x C2R: thread j ends holding y[j + s Q/8] = H(2n) + i H(2n+1),
+//      n = j + s Q/8, i.e. H_demag at cells 2n, 2n+1 (s < 4), written to shared memory;
+//   3. cell update (exchange, anisotropy, Zeeman, Eq. 3, renormalise) with a coalesced
+//      mapping, cells in pairs with 8-byte global accesses; the new Ms m goes back to
+//      shared memory;
+//   4. x R2C of Ms m_{n+1} (zero upper half) and the Hermitian split, X_k and X_{Q-k}
+//      from one pair of loads, stored to S for the next step's y-z pass.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -20,17 +23,18 @@
 namespace grace {
 namespace fastx {
 
-// Line-buffer stride for TY y lines of 3 components (line (t, c) at (3 t + c) * LS):
-// the staging and store loops run t fastest, so 3 LS must put the TY lines of one k on
-// different bank pairs; the FFT exchanges run j fastest within one line.
+// Line-buffer stride for TY y lines of 3 components (line (t, c) at (3 t + c) * LS): the
+// split reads the TY lines of one k together, so 3 LS puts them on different bank pairs;
+// the FFT exchanges run j fastest within one line.
 __host__ __device__ constexpr int x_line_stride(int Q, int TY) {
   return fast_line_stride(Q, TY >= 4 ? 12 : (TY == 2 ? 8 : 0));
 }
 
-// Shared memory: 3 TY line buffers (x_line_stride float2 each) for staging, the Hermitian
-// merge / split and the FFT exchanges; hs[3][TY][Q] floats, holding H_demag per cell and,
-// after the update, Ms m of the new state, lies over the same bytes (the line buffers are
-// idle between the inverse transform and the forward one).
+// Shared memory: 3 TY line buffers (x_line_stride float2 each) for the FFT exchanges and
+// the split.  Over the same bytes, at different times: the staged spectrum st[c][k][t]
+// (read by the merge before the first exchange) and hs[3][TY][Q] floats, holding H_demag
+// per cell and, after the update, Ms m of the new state (the line buffers are idle
+// between the inverse transform and the forward one).
 // y lines per block: 256 threads where the line allows, at most 4 lines
 __host__ __device__ constexpr int x_tile(int Q) {
   return (256 / (Q / 8)) < 1 ? 1 : ((256 / (Q / 8)) > 4 ? 4 : 256 / (Q / 8));

@@ -3,10 +3,11 @@
 // direct sum along z (the zero-padded z convolution of Sec. 3 written out for thin
 // films), the inverse y FFT and the crop back to ny rows.
 //
-// Block = KPB kx columns x 3 nz lines x Py/8 threads per line.  The forward FFT starts
+// Block = KPB kx columns x nz z rows x Py/8 threads per row, each thread transforming the
+// 3 field components of its row (3 x 8 points in registers).  The forward FFT starts
 // from registers loaded straight from S and the inverse ends in registers stored
 // straight to S; shared memory carries the FFT exchanges and the transpose that gives
-// one thread all 3 nz values of one (kx, ky) for the tensor product.
+// one thread all 3 nz values of one (kx, ky) and of its mirror ky for the tensor product.
 #include <cuda_runtime.h>
 
 #include "fftreg.cuh"
