@@ -47,6 +47,10 @@ class _Base:
         self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8,
                                      device=self.device)
         self.stream = stream
+        if stream is not None:
+            # the handle's work runs on `stream`: the allocator must not hand the workspace
+            # out again before that work is done
+            self.workspace.record_stream(stream)
         check(self._L.grace_bind(ctx, self.workspace.data_ptr(), self.workspace_bytes,
                                  _stream_ptr(stream)), "grace_bind", ctx)
         self._keep = {}
@@ -58,6 +62,8 @@ class _Base:
     def get_m(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         if out is None:
             out = torch.empty(3 * self.ncell, dtype=torch.float32, device=self.device)
+            if self.stream is not None:
+                out.record_stream(self.stream)   # written on the handle's stream
         check(self._L.grace_get_m(self.ctx, _dev_ptr(out, 3 * self.ncell, "out")), "grace_get_m",
               self.ctx)
         return out
@@ -128,6 +134,8 @@ class _Base:
     def heff(self, mask: int = TERM_ALL, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         if out is None:
             out = torch.empty(3 * self.ncell, dtype=torch.float32, device=self.device)
+            if self.stream is not None:
+                out.record_stream(self.stream)   # written on the handle's stream
         check(self._L.grace_heff(self.ctx, _dev_ptr(out, 3 * self.ncell, "out"), mask), "grace_heff",
               self.ctx)
         return out
@@ -147,6 +155,10 @@ class _Base:
               "grace_backward_workspace_size", self.ctx)
         scratch = torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=self.device)
         gm0 = torch.empty(3 * self.ncell, dtype=torch.float32, device=self.device) if want_m0 else None
+        if self.stream is not None:
+            for t in (scratch, gm0):
+                if t is not None:
+                    t.record_stream(self.stream)
         check(self._L.grace_backward(
             self.ctx, _dev_ptr(dL_dmT, 3 * self.ncell, "dL/dm_T"), int(n), float(dt), int(ckpt_every),
             scratch.data_ptr(), int(sz.value),
