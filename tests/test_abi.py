@@ -131,3 +131,10 @@ def test_pulse_and_time_validation(lib):
     assert lib.grace_set_time(ctx, float("inf")) == EINVAL
     assert lib.grace_get_time(ctx, None) == EINVAL
     assert lib.grace_destroy(ctx) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without libgrace.so the binding raises instead of computing."""
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load(str(tmp_path / "libgrace.so"))
