@@ -183,7 +183,9 @@ class ClockSampler:
 
 
 def algorithmic_bytes(g, film):
-    """Compulsory bytes of one launch of each kernel (each operand read once, result written once)."""
+    """Compulsory bytes of one launch of each kernel (each operand read once, result written
+    once).  Films with nz <= 4 take the fused path (x pass, fused y pass with the direct z
+    sum); thicker ones the split path (x pass, y FFT launched forward and inverse, z pass)."""
     nx, ny, nz = film.grid
     Px = 1
     while Px < 2 * nx - 1:
@@ -192,13 +194,39 @@ def algorithmic_bytes(g, film):
     while Py < 2 * ny - 1:
         Py *= 2
     Kx, Ky = Px // 2 + 1, Py // 2 + 1
-    nslot = 4 if nz == 1 else 6 * nz - 2
     N = nx * ny * nz
-    spec = 3 * nz * Kx * ny * 8
-    tensor = Kx * nslot * Ky * 4
-    return {"yz_fast": 2 * spec + tensor,          # read S and T, write S
-            "x_fast": 2 * spec + 2 * 12 * N,       # read S and m, write S and m
-            "per_cell": (4 * spec + tensor + 24 * N) / N}
+    spec = 3 * nz * Kx * ny * 8                    # x-transformed rows: [3][nz][Kx][ny] complex
+    x_fast = 2 * spec + 2 * 12 * N                 # read S and m, write S and m
+    if nz <= 4:
+        nslot = 4 if nz == 1 else 6 * nz - 2
+        tensor = Kx * nslot * Ky * 4
+        return {"yz_fast": 2 * spec + tensor,      # read S and T, write S
+                "x_fast": x_fast,
+                "per_cell": (4 * spec + tensor + 24 * N) / N}
+    Pz = 1
+    while Pz < 2 * nz - 1:
+        Pz *= 2
+    A1, A2 = Kx * ny * nz, Kx * Py * nz
+    tensor = Kx * Ky * (Pz // 2 + 1) * 6 * 4
+    y_fast = 24 * A1 + 24 * A2                     # either direction: ny rows <-> Py rows
+    z_fast = 48 * A2 + tensor                      # read and write the Py rows, read T
+    return {"x_fast": x_fast, "y_fast": y_fast, "z_fast": z_fast,
+            "per_cell": (x_fast + 2 * y_fast + z_fast) / N}
+
+
+def kernel_rooflines(trace, byt, peak, peak_kind, workload):
+    """Per traced kernel: average launch time, algorithmic bytes per launch, achieved GB/s
+    and its fraction of the HBM peak, and the profiled DRAM bytes per launch (or None)."""
+    out = {}
+    for k, (ms, n) in trace.items():
+        if k not in byt:
+            continue
+        avg = ms / n * 1e-3
+        gbs = byt[k] / avg / 1e9
+        out[k] = {"launches": n, "avg_launch_us": round(avg * 1e6, 2), "bytes_per_launch": byt[k],
+                  "achieved": round(gbs, 1), "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                  "frac": round(gbs / peak, 4), "traffic": recorded_traffic(k, workload)}
+    return out
 
 
 def five_pass_bytes(film):
@@ -428,9 +456,20 @@ def extra_workloads(dev):
     t = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
     tr = g.trace_read()
     g.trace(0)
+    peak, peak_kind = measured_peaks()
+    byt = algorithmic_bytes(g, f)
+    step_s = t / 20
     out["block"] = {"workload": w.name, "value": f.ncells * 20 / t, "unit": UNIT, "ms_per_step": t / 20 * 1e3,
                     "kernels_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in tr.items()},
-                    "method": "20 single steps, L2 flushed before each"}
+                    "roofline": kernel_rooflines(tr, byt, peak, peak_kind, "block"),
+                    "step_roofline": {
+                        "unit": "GB/s", "peak": peak, "peak_source": peak_kind,
+                        "bytes_split": int(byt["per_cell"] * f.ncells),
+                        "frac_split": round(byt["per_cell"] * f.ncells / step_s / 1e9 / peak, 4),
+                        "bytes_five_pass_model": int(five_pass_bytes(f)),
+                        "frac_five_pass_model": round(five_pass_bytes(f) / step_s / 1e9 / peak, 4)},
+                    "method": "20 single steps, L2 flushed before each; kernel times from the "
+                              "traced steps"}
     del g
     # 256-film ensemble, 2000 steps in replayed CUDA graphs (one grouped launch per kernel
     # and size class per step)
@@ -440,8 +479,16 @@ def extra_workloads(dev):
     gb.step(32, w.dt)
     t = time_events(lambda: gb.step(2000, w.dt), 1)
     ncell = sum(f.ncells for f in w.films)
+    fused_b = sum(algorithmic_bytes(None, fi)["per_cell"] * fi.ncells for fi in w.films)
+    model_b = sum(five_pass_bytes(fi) for fi in w.films)
+    step_s = t / 2000
     out["ensemble"] = {"workload": w.name, "films": len(w.films), "cells": ncell,
                        "value": ncell * 2000 / t, "unit": UNIT, "ms_per_step": t / 2000 * 1e3,
+                       "step_roofline": {
+                           "unit": "GB/s", "peak": peak, "peak_source": peak_kind,
+                           "bytes_fused": int(fused_b), "frac_fused": round(fused_b / step_s / 1e9 / peak, 4),
+                           "bytes_five_pass_model": int(model_b),
+                           "frac_five_pass_model": round(model_b / step_s / 1e9 / peak, 4)},
                        "method": "2000 steps back to back (graphs of 16 steps); ~300 MB working set"}
     del gb
     # adjoint film: 256 forward steps, then the backward pass (checkpoints every 64)

@@ -30,6 +30,35 @@ def test_fused_bytes_of_film_large():
     assert b["per_cell"] == pytest.approx((4 * S + T + 24 * N) / N)
 
 
+def test_split_path_bytes_of_the_block():
+    """256x256x64 block (split path): x pass as above; y FFT either way: ny rows in, Py rows
+    out (or back); z pass: read and write the Py rows and read the 6-component octant."""
+    f = workloads.block().films[0]
+    b = bench.algorithmic_bytes(None, f)
+    N = 256 * 256 * 64
+    Kx, Ky, Kz = 257, 257, 65
+    A1, A2 = Kx * 256 * 64, Kx * 512 * 64
+    assert b["x_fast"] == 2 * 24 * A1 + 24 * N
+    assert b["y_fast"] == 24 * A1 + 24 * A2
+    assert b["z_fast"] == 48 * A2 + Kx * Ky * Kz * 6 * 4
+    assert b["per_cell"] * N / 1e6 == pytest.approx(1416.37788, rel=1e-9)
+    # the split path moves the five-pass bytes less one extra read of m
+    assert bench.five_pass_bytes(f) - b["per_cell"] * N == pytest.approx(12 * N)
+
+
+def test_kernel_rooflines():
+    f = workloads.block().films[0]
+    byt = bench.algorithmic_bytes(None, f)
+    r = bench.kernel_rooflines({"y_fast": (2.2, 40), "other": (1.0, 1)}, byt, 6000.0, "measured",
+                               "no_such_workload")
+    assert set(r) == {"y_fast"}
+    y = r["y_fast"]
+    assert y["avg_launch_us"] == pytest.approx(55.0)
+    assert y["achieved"] == pytest.approx(byt["y_fast"] / 55e-6 / 1e9, abs=0.05)
+    assert y["frac"] == pytest.approx(y["achieved"] / 6000.0, abs=1e-4)
+    assert y["traffic"] is None
+
+
 def test_peak_lookup(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_peaks() == (6800.0, "fallback")
