@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-procs", type=int, default=-1,
+                    help="oracle replicas for the all-cores CPU figure (-1: every host core, 0: skip)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the block / ensemble / adjoint measurements")
     ap.add_argument("--profile-run", default=None, choices=["film_large", "block", "film_small", "adjoint_film"],
@@ -398,6 +400,8 @@ def run_grace(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds)
+        if args.cpu_procs != 0:
+            cpu["all_cores"] = cpu_baseline_all_cores(args.workload, args.cpu_seconds, args.cpu_procs)
     launches = sum(v[1] for v in trace.values()) // max(1, ktr) * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -610,6 +614,76 @@ def cpu_baseline(w, seconds):
     return {"value": f.ncells * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} FP64 Euler steps of the full {w.name} film (numpy FFT convolution, "
                       f"single thread), {dt:.1f} s", "steps": n, "seconds": dt}
+
+
+def _oracle_replica(name, seconds, barrier, results):
+    """One oracle replica (a spawned process): its own film and tensor spectrum, then Euler
+    steps for `seconds` once every replica is ready."""
+    import numpy as np
+
+    import workloads
+    from oracle import llg
+    w = getattr(workloads, name)()
+    f, m0 = w.films[0], w.m0[0]
+    p = llg.Params(f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, f.hext)
+    D = llg.Demag(f.grid, f.cell)
+    m = m0.astype(np.float64)
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        m = llg.euler_step(m, p, w.dt, D)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    results.put((n, time.perf_counter() - t0, f.ncells))
+
+
+def cpu_baseline_all_cores(name, seconds, procs=-1):
+    """The same oracle on every host core: independent replicas of the workload in spawned
+    processes (the oracle itself is single-threaded), timed over a common window.  The
+    replica count is capped by the host memory (about 2 GB per film_large replica)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    n = cores if procs < 0 else min(procs, cores)
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        n = max(1, min(n, int(avail // (2 << 30))))
+    except (ValueError, OSError, AttributeError):
+        pass
+    ctx = mp.get_context("spawn")             # never fork a process that holds a CUDA context
+    barrier, results = ctx.Barrier(n), ctx.Queue()
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ.update({k: "1" for k in env})
+    import queue
+    ps, out = [], []
+    try:
+        ps = [ctx.Process(target=_oracle_replica, args=(name, seconds, barrier, results)) for _ in range(n)]
+        for p in ps:
+            p.start()
+        deadline = time.time() + 900
+        while len(out) < n:
+            try:
+                out.append(results.get(timeout=2))
+            except queue.Empty:
+                if time.time() > deadline or any(p.exitcode not in (None, 0) for p in ps):
+                    return {"unavailable": "an oracle replica failed or did not finish", "cores": n}
+        for p in ps:
+            p.join()
+    finally:
+        for p in ps:                          # only the replicas started here
+            if p.is_alive():
+                p.terminate()
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    steps = sum(o[0] for o in out)
+    value = sum(o[0] * o[2] / o[1] for o in out)
+    return {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "replicas": n,
+            "sample": f"{n} single-threaded oracle replicas of the full {name} film, one per core, "
+                      f"{steps} FP64 Euler steps in all over ~{seconds:.0f} s"}
 
 
 def run_reference(args, rank, world):

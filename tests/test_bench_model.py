@@ -75,3 +75,12 @@ def test_recorded_traffic_follows_the_kernel_sources():
         assert got == rec["kernels"]["film_large"]["x_fast"]
     else:
         assert got is None
+
+
+def test_all_cores_oracle_replicas():
+    """Spawned single-threaded oracle replicas over a common window: every replica reports,
+    and the aggregate is the sum of their rates."""
+    r = bench.cpu_baseline_all_cores("film_small", 1.0, 2)
+    assert r["cores"] == r["replicas"] == 2
+    assert r["kind"] == "oracle" and r["unit"] == bench.UNIT
+    assert r["value"] > 0
