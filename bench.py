@@ -52,28 +52,48 @@ def parse():
                     help="oracle replicas for the all-cores CPU figure (-1: every host core, 0: skip)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the block / ensemble / adjoint measurements")
-    ap.add_argument("--profile-run", default=None, choices=["film_large", "block", "film_small", "adjoint_film"],
+    ap.add_argument("--profile-run", default=None,
+                    choices=["film_large", "block", "film_small", "adjoint_film", "ensemble"],
                     help="no measurement: take --steps plain-launch steps of this workload (for ncu)")
     return ap.parse_args()
 
 
 def profile_run(name, steps):
-    """Plain launches (no graphs) of `steps` steps, so that a profiler sees every kernel."""
+    """Plain launches (no graphs) of `steps` steps, so that a profiler sees every kernel.
+    ensemble: the 256-film batch; adjoint_film: `steps` forward steps, then the discrete
+    adjoint of those steps (checkpoints every 16)."""
+    import numpy as np
     import torch
     import workloads
     from paper_1411_2565_gb300 import _lib
     from paper_1411_2565_gb300.build import build
-    from paper_1411_2565_gb300.grace import Grace
+    from paper_1411_2565_gb300.grace import Grace, GraceBatch
     build()
     w = getattr(workloads, name)()
+    opts = {_lib.OPT_GRAPH: 0}
+    if name == "ensemble":
+        g = GraceBatch(w.films, device="cuda:0", options=opts)
+        g.set_m(torch.from_numpy(np.concatenate([m.reshape(-1) for m in w.m0])).cuda())
+        g.step(steps, w.dt)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": name, "steps": steps}), flush=True)
+        return
     f, m0 = w.films[0], w.m0[0]
-    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device="cuda:0",
-              options={_lib.OPT_GRAPH: 0})
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device="cuda:0", options=opts)
     g.set_hext(f.hext)
     if getattr(w, "ms_field", None) is not None:
         g.set_ms_field(torch.from_numpy(w.ms_field.reshape(-1)).cuda())
-    g.set_m(torch.from_numpy(m0.reshape(-1)).cuda())
+    if name == "adjoint_film":
+        g.set_hext_field(torch.zeros(3 * f.ncells, device="cuda:0"))
+    md = torch.from_numpy(m0.reshape(-1)).cuda()
+    g.set_m(md)
     g.step(steps, w.dt)
+    if name == "adjoint_film":
+        lam = torch.full((3 * f.ncells,), 1e-6, device="cuda:0")
+        gh = torch.zeros(3 * f.ncells, device="cuda:0")
+        gm = torch.zeros(f.ncells, device="cuda:0")
+        g.set_m(md)
+        g.backward(lam, steps, w.dt, 16, gh, gm)
     torch.cuda.synchronize()
     print(json.dumps({"profile_run": name, "steps": steps}), flush=True)
 
