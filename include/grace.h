@@ -41,8 +41,9 @@ typedef struct grace_ctx grace_ctx;
 
 typedef enum {
   GRACE_OK = 0,
-  GRACE_EINVAL = -1,       /* bad argument: NULL, n_d < 1, n_d > 2048, cell <= 0, Ms <= 0, A < 0,
-                              alpha < 0, gamma0 <= 0, dt <= 0, n < 0, unknown option/term bits */
+  GRACE_EINVAL = -1,       /* bad argument: NULL, n_d < 1, n_d > 2048, more than 715,827,882
+                              cells in a film, cell <= 0, Ms <= 0, A < 0, alpha < 0,
+                              gamma0 <= 0, dt <= 0, n < 0, unknown option/term bits */
   GRACE_EWORKSPACE = -2,   /* workspace smaller than grace_workspace_size or misaligned */
   GRACE_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
   GRACE_ETIMEOUT = -4,     /* reserved: a bounded device-side wait expired */
@@ -90,7 +91,8 @@ enum {
 
 /*
  * grace_create - plan one rectangular film (Sec. 2: regular cell grid; Sec. 4 workloads).
- *   grid[3]   cells (nx, ny, nz), each 1..2048.
+ *   grid[3]   cells (nx, ny, nz), each 1..2048, at most 715,827,882 cells in all (the
+ *             kernels index the 3 N components of a film with 32-bit integers).
  *   cell_m[3] cell size (dx, dy, dz) in metres, > 0.
  *   Ms        saturation magnetisation (A/m, > 0); a per-cell field may replace it
  *             (grace_set_ms_field).

@@ -135,6 +135,13 @@ bool valid_film(const int n[3], const double cell[3], double Ms, double A, doubl
       why = "grid dimension out of range 1..2048";
       return false;
     }
+  }
+  // the kernels address a film's 3 N components with 32-bit indices (c N + i)
+  if (3LL * n[0] * n[1] * n[2] > 2147483647LL) {
+    why = "more than 715827882 cells in one film";
+    return false;
+  }
+  for (int d = 0; d < 3; ++d) {
     if (!(cell[d] > 0.0) || !std::isfinite(cell[d])) {
       why = "cell size must be positive";
       return false;
@@ -362,20 +369,23 @@ int plan(grace_ctx* c) {
   }
   c->ncell = cell0;
   for (auto& g : c->groups) {
-    int u[UK_COUNT] = {0, 0, 0, 0, 0};
+    long long u[UK_COUNT] = {0, 0, 0, 0, 0};
     for (int i : g.idx) {
       FilmDev& d = c->fd[i];
-      d.u0[UK_X] = u[UK_X];
-      u[UK_X] += d.nz * ((d.ny + g.TY - 1) / g.TY);
-      d.u0[UK_YZ] = u[UK_YZ];
+      d.u0[UK_X] = (int)u[UK_X];
+      u[UK_X] += (long long)d.nz * ((d.ny + g.TY - 1) / g.TY);
+      d.u0[UK_YZ] = (int)u[UK_YZ];
       u[UK_YZ] += (g.fast && !g.split_fast) ? (d.Kx + g.KPB - 1) / g.KPB : d.Kx;
-      d.u0[UK_Y] = u[UK_Y];
-      u[UK_Y] += (3 * d.nz * d.Kx + g.RPB - 1) / g.RPB;
-      d.u0[UK_Z] = u[UK_Z];
-      u[UK_Z] += (d.Kx * d.Py + g.TQ - 1) / g.TQ;
+      d.u0[UK_Y] = (int)u[UK_Y];
+      u[UK_Y] += (3LL * d.nz * d.Kx + g.RPB - 1) / g.RPB;
+      d.u0[UK_Z] = (int)u[UK_Z];
+      u[UK_Z] += ((long long)d.Kx * d.Py + g.TQ - 1) / g.TQ;
       d.u0[UK_CELL] = 0;
+      // block indices and unit offsets are 32-bit (grid x dimension)
+      for (int k = 0; k < UK_COUNT; ++k)
+        if (u[k] > 2147483647LL) return GRACE_EINVAL;
     }
-    for (int k = 0; k < UK_COUNT; ++k) g.units[k] = u[k];
+    for (int k = 0; k < UK_COUNT; ++k) g.units[k] = (int)u[k];
   }
 
   // workspace layout: [twiddles | descriptors | tensors | runtime (aliased by build scratch)]

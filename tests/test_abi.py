@@ -42,7 +42,8 @@ def _create(lib, grid=(16, 8, 2), cell=(3e-9, 3e-9, 3e-9), Ms=8e5, A=1.3e-11, Ku
 
 
 @pytest.mark.parametrize("kw", [dict(grid=(0, 8, 2)), dict(grid=(16, 8, 4097)), dict(grid=(2049, 1, 1)),
-                                dict(grid=(1, 2049, 1)), dict(grid=(1, 1, 2049)), dict(grid=(-1, 1, 1)), dict(cell=(0, 1e-9, 1e-9)),
+                                dict(grid=(1, 2049, 1)), dict(grid=(1, 1, 2049)), dict(grid=(-1, 1, 1)),
+                                dict(grid=(2048, 2048, 2048)), dict(grid=(1024, 1024, 683)), dict(cell=(0, 1e-9, 1e-9)),
                                 dict(Ms=0.0), dict(Ms=-1.0), dict(A=-1e-11), dict(alpha=-0.1),
                                 dict(g0=0.0), dict(Ms=float("nan"))])
 def test_create_rejects_invalid_arguments(lib, kw):
@@ -52,7 +53,9 @@ def test_create_rejects_invalid_arguments(lib, kw):
 
 
 def test_largest_axis_is_accepted(lib):
-    for grid in [(2048, 1, 1), (1, 2048, 1), (1, 1, 2048)]:
+    """Each axis up to 2048 cells, and films up to 715,827,882 cells (3 N within 32-bit
+    indexing) are planned."""
+    for grid in [(2048, 1, 1), (1, 2048, 1), (1, 1, 2048), (1024, 1024, 682)]:
         st, ctx = _create(lib, grid=grid)
         assert st == 0
         assert lib.grace_destroy(ctx) == 0
