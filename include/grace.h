@@ -111,7 +111,9 @@ int grace_create(grace_ctx **out, const int grid[3], const double cell_m[3], dou
  * grace_step (without a time envelope) the groups run side by side on streams of their
  * own, forked from and joined back into the bound stream.  Arrays hold nfilms entries
  * (grid and cell_m: 3 per film, row-major).  Films with the same (grid, cell) share one
- * demag tensor.  Same validation as grace_create for every film; nfilms in 1..65536.
+ * demag tensor.  Same validation as grace_create for every film; nfilms in 1..65536;
+ * GRACE_EINVAL also when a group of films would need more than 2^31 - 1 thread blocks
+ * in one launch.
  */
 int grace_batch_create(grace_ctx **out, int nfilms, const int *grid, const double *cell_m,
                        const double *Ms, const double *A, const double *Ku,
