@@ -78,6 +78,24 @@ def test_create_plans_workspace_and_counts_cells(lib):
     lib.grace_destroy(ctx)
 
 
+def test_workspace_of_the_largest_film_does_not_wrap(lib):
+    """1024 x 1024 x 682 cells (the largest cell count a film may have along these axes):
+    the workspace is planned in 64-bit sizes (spectrum with Py rows, FFT-z tensor, four
+    state-sized arrays)."""
+    st, ctx = _create(lib, grid=(1024, 1024, 682), cell=(2e-9,) * 3)
+    assert st == 0
+    sz = C.c_size_t()
+    assert lib.grace_workspace_size(ctx, C.byref(sz)) == 0
+    N = 1024 * 1024 * 682
+    Kx, Py, Ky, Kz = 1025, 2048, 1025, 1025
+    spectrum = 3 * 682 * Kx * Py * 8
+    tensor = Kx * Ky * (6 * Kz) * 4
+    state = 4 * 3 * N * 4
+    assert sz.value >= spectrum + tensor + state > 2 ** 36
+    assert sz.value < 2 * (spectrum + tensor + state)
+    lib.grace_destroy(ctx)
+
+
 def test_call_order_and_workspace_checks(lib):
     st, ctx = _create(lib)
     assert st == 0
