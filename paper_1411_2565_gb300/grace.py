@@ -175,9 +175,17 @@ class _Base:
         return dict(zip(names, list(e))), np.array(list(mv))
 
     def close(self):
+        """Release the handle (its streams, events and graphs); the tensors stay with torch."""
         if getattr(self, "ctx", None):
             self._L.grace_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     def __del__(self):
         try:
