@@ -12,7 +12,15 @@ because the film's working set (~100 MB) fits in the 129 MB L2.
 For N > 1 (torchrun, one process per GPU) every rank steps its own replica of the film
 (replicas only: the workload has no data exchange), value = all ranks' cell-steps / the
 slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle (the only reference
-implementation: the paper's own code is not available) on rank 0.
+implementation: the paper's own code is not available) on rank 0, one single-threaded
+replica of the film per host core.
+
+Beside the headline the line carries the x pass's HBM roofline, the whole step against
+the same peak, end-to-end throughput from host buffers, the oracle on one and on all host
+cores, the SM clocks sampled during the timed loop, and (unless ``--no-extras``) the thick
+block, the 256-film ensemble and the adjoint with their own rooflines, the paper-shaped
+cube sweep and a vendor-FFT demag comparison.  ``--profile-run NAME`` only takes plain-
+launch steps of a workload, for ncu.
 
 Prints one JSON line.
 """
