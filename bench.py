@@ -18,8 +18,8 @@ replica of the film per host core.
 Beside the headline the line carries the x pass's HBM roofline, the whole step against
 the same peak, end-to-end throughput from host buffers, the oracle on one and on all host
 cores, the SM clocks sampled during the timed loop, and (unless ``--no-extras``) the thick
-block, the 256-film ensemble and the adjoint with their own rooflines, the paper-shaped
-cube sweep and a vendor-FFT demag comparison.  ``--profile-run NAME`` only takes plain-
+block and the 256-film ensemble with their own rooflines, the adjoint's forward and
+backward rates, the paper-shaped cube sweep and a vendor-FFT demag comparison.  ``--profile-run NAME`` only takes plain-
 launch steps of a workload, for ncu.
 
 Prints one JSON line.
