@@ -1,13 +1,16 @@
 """Benchmark: LLG cell-steps/s of the full H_eff + Euler step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grace|reference]
-                    [--workload film_large|block|film_small]
+                    [--workload block|film_large|film_small]
 
-One "step" is one pass of the hot path over the film: demag convolution (fused y pass
-and x C2R), exchange, anisotropy, Zeeman, explicit Euler with renormalisation and the
-x R2C of the new state (two kernels per step).  Inputs are resident in HBM when the
-timed region starts; every timed step is preceded by an L2 flush (a 256 MiB write)
-because the film's working set (~100 MB) fits in the 129 MB L2.
+The headline workload is the 256x256x64 block (4.19 M cells of 3 nm, padded grid
+512x512x128), the largest single-GPU configuration.  One "step" is one pass of the hot
+path over it: the demag convolution (x C2R, y FFT, z FFT with the tensor product, and
+their inverses), exchange, anisotropy, Zeeman, explicit Euler with renormalisation and
+the x R2C of the new state (four kernels per step on this split path; films of at most
+four cells in z take two).  Inputs are resident in HBM when the timed region starts;
+every timed step is preceded by an L2 flush (a 256 MiB write), so no step finds the
+previous one's data in the 129 MB L2.
 
 For N > 1 (torchrun, one process per GPU) every rank steps its own replica of the film
 (replicas only: the workload has no data exchange), value = all ranks' cell-steps / the
@@ -15,12 +18,13 @@ slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle (the only r
 implementation: the paper's own code is not available) on rank 0, one single-threaded
 replica of the film per host core.
 
-Beside the headline the line carries the x pass's HBM roofline, the whole step against
-the same peak, end-to-end throughput from host buffers, the oracle on one and on all host
-cores, the SM clocks sampled during the timed loop, and (unless ``--no-extras``) the thick
-block and the 256-film ensemble with their own rooflines, the adjoint's forward and
-backward rates, the paper-shaped cube sweep and a vendor-FFT demag comparison.  ``--profile-run NAME`` only takes plain-
-launch steps of a workload, for ncu.
+Beside the headline the line carries the dominant kernel's HBM roofline, the whole step
+against the same peak, end-to-end throughput from host buffers, the oracle on one and on
+all host cores, the SM clocks sampled during the timed loop, and (unless ``--no-extras``)
+the 1024x256x4 film with its own rooflines, the 256-film ensemble, the adjoint's forward
+and backward rates at its stated 4,096 steps, the paper-shaped cube sweep and a
+vendor-FFT demag comparison.  ``--profile-run NAME`` only takes plain-launch steps of a
+workload, for ncu.
 
 Prints one JSON line.
 """
@@ -52,7 +56,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="grace", choices=["grace", "reference"])
-    ap.add_argument("--workload", default="film_large", choices=["film_large", "block", "film_small"])
+    ap.add_argument("--workload", default="block", choices=["block", "film_large", "film_small"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -361,14 +365,15 @@ def run_grace(args, rank, world, local):
     # dominant kernel and its roofline
     peak, peak_kind = measured_peaks()
     byt = algorithmic_bytes(g, f)
-    # the whole step against the HBM peak: the bytes this design moves (x pass + fused y-z
-    # pass, each array read and written once) and, for comparison, the five-pass model
-    # (x, y, z FFT passes with every intermediate spectrum in HBM)
+    # the whole step against the HBM peak: `frac_moved` takes the bytes this design moves
+    # (every kernel's arrays read and written once) and is the step's roofline fraction;
+    # `frac_five_pass_model` (every intermediate spectrum through HBM, bytes this design
+    # does not move) is only a labelled comparison
     step_s = total_ms * 1e-3 / args.steps
-    fused_b = byt["per_cell"] * ncell
+    moved_b = byt["per_cell"] * ncell
     model_b = five_pass_bytes(f)
     step_roof = {"unit": "GB/s", "peak": peak, "peak_source": peak_kind, "step_us": round(step_s * 1e6, 2),
-                 "bytes_fused": int(fused_b), "frac_fused": round(fused_b / step_s / 1e9 / peak, 4),
+                 "bytes_moved": int(moved_b), "frac_moved": round(moved_b / step_s / 1e9 / peak, 4),
                  "bytes_five_pass_model": int(model_b),
                  "frac_five_pass_model": round(model_b / step_s / 1e9 / peak, 4)}
     dom = max(trace.items(), key=lambda kv: kv[1][0])[0] if trace else None
@@ -424,7 +429,7 @@ def run_grace(args, rank, world, local):
 
     extras = None
     if rank == 0 and not args.no_extras:
-        extras = extra_workloads(dev)
+        extras = extra_workloads(dev, args.workload)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds)
@@ -462,23 +467,21 @@ def time_events(fn, reps):
     return a.elapsed_time(b) * 1e-3
 
 
-def extra_workloads(dev):
-    """Throughput of the other forms of the hot path (thick block, film ensemble, adjoint)."""
-    import numpy as np
+def plain_workload_extra(dev, name, flush, steps=200):
+    """Another plain single-film workload beside the headline: `steps` single steps with L2
+    flushed before each, the per-kernel split from traced steps, per-kernel rooflines and
+    the whole step against the HBM peak."""
     import torch
 
     import workloads
-    from paper_1411_2565_gb300.grace import Grace, GraceBatch
-    out = {}
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    # 256x256x64 block, FFT along z: 20 single steps, L2 flushed before each
-    w = workloads.block()
+    from paper_1411_2565_gb300.grace import Grace
+    w = getattr(workloads, name)()
     f, m0 = w.films[0], w.m0[0]
     g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=dev)
+    g.set_hext(f.hext)
     g.set_m(torch.from_numpy(m0.reshape(-1)).to(dev))
-    g.step(3, w.dt)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
-    g.trace(200)
+    g.step(5, w.dt)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for a, b in ev:
         flush.zero_()
         a.record()
@@ -486,23 +489,44 @@ def extra_workloads(dev):
         b.record()
     torch.cuda.synchronize()
     t = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    g.trace(8 * steps)
+    for _ in range(steps):
+        flush.zero_()
+        g.step(1, w.dt)
     tr = g.trace_read()
     g.trace(0)
+    g.close()
     peak, peak_kind = measured_peaks()
     byt = algorithmic_bytes(g, f)
-    step_s = t / 20
-    out["block"] = {"workload": w.name, "value": f.ncells * 20 / t, "unit": UNIT, "ms_per_step": t / 20 * 1e3,
-                    "kernels_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in tr.items()},
-                    "roofline": kernel_rooflines(tr, byt, peak, peak_kind, "block"),
-                    "step_roofline": {
-                        "unit": "GB/s", "peak": peak, "peak_source": peak_kind,
-                        "bytes_split": int(byt["per_cell"] * f.ncells),
-                        "frac_split": round(byt["per_cell"] * f.ncells / step_s / 1e9 / peak, 4),
-                        "bytes_five_pass_model": int(five_pass_bytes(f)),
-                        "frac_five_pass_model": round(five_pass_bytes(f) / step_s / 1e9 / peak, 4)},
-                    "method": "20 single steps, L2 flushed before each; kernel times from the "
-                              "traced steps"}
-    del g
+    step_s = t / steps
+    moved = byt["per_cell"] * f.ncells
+    return {"workload": w.name, "value": f.ncells * steps / t, "unit": UNIT,
+            "ms_per_step": step_s * 1e3,
+            "kernels_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in tr.items()},
+            "roofline": kernel_rooflines(tr, byt, peak, peak_kind, name),
+            "step_roofline": {
+                "unit": "GB/s", "peak": peak, "peak_source": peak_kind, "bytes_moved": int(moved),
+                "frac_moved": round(moved / step_s / 1e9 / peak, 4),
+                "bytes_five_pass_model": int(five_pass_bytes(f)),
+                "frac_five_pass_model": round(five_pass_bytes(f) / step_s / 1e9 / peak, 4)},
+            "method": f"{steps} single steps, L2 flushed before each; kernel times from "
+                      f"{steps} more traced steps"}
+
+
+def extra_workloads(dev, headline):
+    """Throughput of the other forms of the hot path: the other plain workload (film or
+    block), the film ensemble, the adjoint, the cube sweep and a vendor-FFT comparison."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_1411_2565_gb300.grace import Grace, GraceBatch
+    out = {}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peak, peak_kind = measured_peaks()
+    for name in ("block", "film_large"):
+        if name != headline:
+            out[name] = plain_workload_extra(dev, name, flush)
     # 256-film ensemble, 2000 steps in replayed CUDA graphs (one grouped launch per kernel
     # and size class per step)
     w = workloads.ensemble()
@@ -518,12 +542,13 @@ def extra_workloads(dev):
                        "value": ncell * 2000 / t, "unit": UNIT, "ms_per_step": t / 2000 * 1e3,
                        "step_roofline": {
                            "unit": "GB/s", "peak": peak, "peak_source": peak_kind,
-                           "bytes_fused": int(fused_b), "frac_fused": round(fused_b / step_s / 1e9 / peak, 4),
+                           "bytes_moved": int(fused_b), "frac_moved": round(fused_b / step_s / 1e9 / peak, 4),
                            "bytes_five_pass_model": int(model_b),
                            "frac_five_pass_model": round(model_b / step_s / 1e9 / peak, 4)},
                        "method": "2000 steps back to back (graphs of 16 steps); ~300 MB working set"}
     del gb
-    # adjoint film: 256 forward steps, then the backward pass (checkpoints every 64)
+    # adjoint film at its stated length: 4,096 forward steps, then the backward pass
+    # (checkpoints every 64)
     w = workloads.adjoint_film()
     f, m0 = w.films[0], w.m0[0]
     g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=dev)
@@ -532,7 +557,7 @@ def extra_workloads(dev):
     g.set_ms_field(ms)
     g.set_hext_field(h)
     md = torch.from_numpy(m0.reshape(-1)).to(dev)
-    n = 256
+    n = w.steps
     g.set_m(md)
     t_f = time_events(lambda: g.step(n, w.dt), 1)
     lam = torch.full((3 * f.ncells,), 1e-6, device=dev)
@@ -544,10 +569,12 @@ def extra_workloads(dev):
     out["adjoint"] = {"workload": w.name, "steps": n, "unit": UNIT,
                       "forward_value": f.ncells * n / t_f, "backward_value": f.ncells * n / t_b,
                       "fwd_plus_bwd_ms_per_step": (t_f + t_b) / n * 1e3,
+                      "backward_over_forward": t_b / t_f,
                       "method": "forward steps, then grace_backward with checkpoints every 64 "
                                 "(re-computes the forward inside)"}
     del g
-    out["cufft_demag_comparison"] = cufft_demag_comparison(dev, flush)
+    out["cufft_demag_comparison"] = {name: cufft_demag_comparison(dev, flush, name)
+                                     for name in ("block", "film_large")}
     out["cube_sweep"] = cube_sweep(dev)
     return out
 
@@ -582,15 +609,15 @@ def cube_sweep(dev, steps=64):
     return res
 
 
-def cufft_demag_comparison(dev, flush, reps=20):
-    """Timed comparison only (not the product path): the film_large demag convolution done
+def cufft_demag_comparison(dev, flush, name="film_large", reps=20):
+    """Timed comparison only (not the product path): a workload's demag convolution done
     with the vendor FFT through torch.fft on the same zero-padded grid, FP32: R2C of the
     three padded components, the 6-component symmetric tensor product, C2R and crop.
     The tensor values are placeholders of the right shape (timing does not depend on them)."""
     import torch
 
     import workloads
-    w = workloads.film_large()
+    w = getattr(workloads, name)()
     f = w.films[0]
     nx, ny, nz = f.grid
     Px, Py, Pz = (1 << (2 * n - 1 - 1).bit_length() if n > 1 else 1 for n in (nx, ny, nz))
@@ -667,16 +694,21 @@ def _oracle_replica(name, seconds, barrier, results):
     results.put((n, time.perf_counter() - t0, f.ncells))
 
 
+# host memory one oracle replica holds (FP64 state, padded FFT buffers, tensor spectrum), bytes
+ORACLE_REPLICA_BYTES = {"block": 7 << 30, "film_large": 2 << 30, "film_small": 1 << 30}
+
+
 def cpu_baseline_all_cores(name, seconds, procs=-1):
     """The same oracle on every host core: independent replicas of the workload in spawned
     processes (the oracle itself is single-threaded), timed over a common window.  The
-    replica count is capped by the host memory (about 2 GB per film_large replica)."""
+    replica count is capped by the host memory (ORACLE_REPLICA_BYTES per replica: about
+    7 GB for the block, 2 GB for film_large)."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     n = cores if procs < 0 else min(procs, cores)
     try:
         avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
-        n = max(1, min(n, int(avail // (2 << 30))))
+        n = max(1, min(n, int(avail // ORACLE_REPLICA_BYTES.get(name, 2 << 30))))
     except (ValueError, OSError, AttributeError):
         pass
     ctx = mp.get_context("spawn")             # never fork a process that holds a CUDA context

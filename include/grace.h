@@ -240,11 +240,14 @@ int grace_trace_read(grace_ctx *ctx, double ms[8], long long counts[8]);
  *               GRACE_TERM_DEMAG).
  *   cuda_stream the stream the work is queued on; the call synchronises it.
  *   out[5], mavg[3] as for grace_energy (either may be NULL).
- * Scratch: per-block FP64 partial sums in one file-scope device array of
- * GRACE_ENERGY_NOALLOC_MAX_CELLS / 4096 * 64 bytes (256 KiB), reserved by every GPU
- * that loads the library until the process exits.  N above GRACE_ENERGY_NOALLOC_MAX_CELLS
- * returns GRACE_EUNSUPPORTED.  The first call on a device looks up that array's device
- * address (with the device current), so make it before any stream capture.  All calls
+ * Scratch: per-block FP64 partial sums and the totals in one file-scope device array
+ * of (GRACE_ENERGY_NOALLOC_MAX_CELLS / 4096 + 1) * 64 bytes (256 KiB + 64 B), held by
+ * every GPU that has loaded the library's device code, until the process exits.  N above
+ * GRACE_ENERGY_NOALLOC_MAX_CELLS returns GRACE_EUNSUPPORTED.  Under CUDA's default lazy
+ * module loading the first call on a device loads that code there, which reserves the
+ * array's device memory and may synchronise, and it looks up the array's device address
+ * (with the device current): make one warm-up call per device at start-up, before any
+ * stream capture and outside any phase that must not allocate.  All calls
  * share the array; each call rewrites every slot it reads, so no clearing is needed, but
  * calls that overlap on the GPU race and must be serialised by the caller.
  * Returns GRACE_EINVAL for bad arguments, GRACE_ECUDA on a CUDA failure,

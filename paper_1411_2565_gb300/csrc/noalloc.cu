@@ -8,8 +8,11 @@
 // loop whose policy forbids allocation after start-up, or code that must not
 // synchronise the device the way cudaMalloc/cudaFree can.  This entry point takes the
 // state m and its demag field as inputs and needs no workspace: its per-block partial
-// sums live in one file-scope device array, reserved when the library is loaded and
-// held by every GPU that loads it until the process exits.
+// sums live in one file-scope device array, held by every GPU that loads the library's
+// device code until the process exits.  Under CUDA's lazy module loading (the default)
+// that code, and with it the array, is loaded on a device by the first call there: that
+// call reserves the array's device memory and may synchronise, so a caller makes one
+// warm-up call at start-up, outside any stream capture or no-allocation phase.
 //
 // The array is shared by all calls.  Every call overwrites each slot it reads (no slot
 // depends on a previous call's contents), so nothing has to be cleared, but calls whose
@@ -26,6 +29,8 @@ namespace {
 
 constexpr int kChunk = 4096;        // cells per block
 constexpr int kMaxChunks = GRACE_ENERGY_NOALLOC_MAX_CELLS / kChunk;
+// every accepted grid (N <= MAX_CELLS) must fit in kMaxChunks chunks, ahead of the totals slot
+static_assert(GRACE_ENERGY_NOALLOC_MAX_CELLS % kChunk == 0, "the cell limit must be a whole number of chunks");
 constexpr int kThreads = 256;
 constexpr double kMu0 = 1.2566370614359172954e-6;
 
@@ -150,6 +155,7 @@ extern "C" int grace_energy_noalloc(const int grid[3], const double cell_m[3], d
   k_energy_chunks<<<nchunks, kThreads, 0, s>>>(f, dev_m, dev_hdemag, scratch);
   k_energy_totals<<<1, 32, 0, s>>>(scratch, nchunks);
   if (cudaGetLastError() != cudaSuccess) return GRACE_ECUDA;
+  // h is pageable stack memory: valid only after the stream synchronisation just below
   double h[8];
   if (cudaMemcpyAsync(h, scratch + (size_t)kMaxChunks * 8, sizeof h, cudaMemcpyDeviceToHost, s) !=
       cudaSuccess)

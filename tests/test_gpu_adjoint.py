@@ -21,6 +21,17 @@ def lib():
     libbuild.build()
 
 
+def _golden_module():
+    """tests/golden/make_adjoint_film_4096.py, loaded by path (tests/ is not a package)."""
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_adjoint_film_4096.py")
+    spec = importlib.util.spec_from_file_location("make_adjoint_film_4096", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
 def rel(a, b):
     a = np.asarray(a, dtype=np.float64).ravel()
     b = np.asarray(b, dtype=np.float64).ravel()
@@ -113,3 +124,37 @@ def test_adjoint_workload_full_grid():
     assert rel(gh.cpu().numpy(), o_h) <= 1e-3
     assert rel(gms.cpu().numpy(), o_ms) <= 1e-3
     assert rel(gm0.cpu().numpy(), o_m0) <= 1e-3
+
+
+def test_adjoint_workload_stated_length():
+    """The adjoint workload at its stated length: 4,096 Euler steps on the 256x64x2 film
+    with checkpoints every 64 (64 recomputed segments), gradients w.r.t. the per-cell
+    applied field, the per-cell Ms and m_0 against the FP64 oracle adjoint of the same
+    4,096 steps (tests/golden/adjoint_film_4096.npz, written by make_adjoint_film_4096.py
+    from the oracle alone)."""
+    gm = _golden_module()
+    OUT, STEPS, inputs_digest = gm.OUT, gm.STEPS, gm.inputs_digest
+    from paper_1411_2565_gb300.grace import Grace
+    w = workloads.adjoint_film()
+    gold = np.load(OUT)
+    assert str(gold["digest"]) == inputs_digest(w), "fixture out of date: rerun its script"
+    f, m0 = w.films[0], w.m0[0]
+    dt, shape = w.dt, f.shape_zyx
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=DEV)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(DEV)
+    g.set_ms_field(dev(w.ms_field))
+    g.set_hext_field(dev(np.zeros((3,) + shape, dtype=np.float32)))
+    g.set_m(dev(m0))
+    g.step(STEPS, dt)
+    mT = g.get_m()
+    n = mT.numel() // 3
+    loss = float(((mT.double() - dev(w.target).double()) ** 2).sum() / n)
+    assert abs(loss - float(gold["loss"])) <= 1e-4 * abs(float(gold["loss"]))
+    lamT = 2.0 * (mT - dev(w.target)) / n
+    g.set_m(dev(m0))
+    gh = torch.zeros(3 * n, device=DEV)
+    gms = torch.zeros(n, device=DEV)
+    gm0 = g.backward(lamT, STEPS, dt, 64, gh, gms)
+    assert rel(gh.cpu().numpy(), gold["g_hext"]) <= 1e-3
+    assert rel(gms.cpu().numpy(), gold["g_ms"]) <= 1e-3
+    assert rel(gm0.cpu().numpy(), gold["g_m0"]) <= 1e-3

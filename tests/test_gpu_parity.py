@@ -216,7 +216,7 @@ def _sampled_cells(grid, rng_seed):
 
 
 @pytest.mark.parametrize("name,after", [("film_large", 0), ("film_large", 100), ("film_large", 1000),
-                                        ("block", 0), ("block", 100)])
+                                        ("block", 0), ("block", 100), ("block", 1000)])
 def test_full_size_sampled_cells(name, after):
     """Full-size workloads in the launch configuration the benchmark times: H_eff and one
     Euler step at sampled cells against the oracle's direct demag sum at those cells, at

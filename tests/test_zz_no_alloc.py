@@ -3,7 +3,8 @@ memory (its FP64 partial sums live in a static device array inside the library).
 
 Checks it through the C ABI against grace_energy, the workspace-based entry point, on
 the same state and demag field, on two calls in a row (the second call must not be
-affected by what the first left in the shared array)."""
+affected by what the first left in the shared array), and the first call also against
+the FP64 oracle's energies."""
 import ctypes as C
 
 import numpy as np
@@ -45,6 +46,14 @@ def test_energy_noalloc_matches_workspace_energy_twice():
         for k, name in enumerate(names):
             assert abs(out[k] - ref[name]) <= REL * scale, (call, name, out[k], ref[name])
         assert np.allclose(list(avg), ref_avg, rtol=0, atol=1e-12)
+        if call == 0:
+            # and directly against the FP64 oracle's Eq. 1 energies of the same state
+            from oracle import llg
+            p = llg.Params(f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, f.hext)
+            oref = llg.energies(m0, p)
+            oscale = max(abs(v) for v in oref[:4])
+            for k in range(5):
+                assert abs(out[k] - oref[k]) <= 2e-6 * oscale + 1e-6 * abs(oref[k]), (k, out[k], oref[k])
 
 
 def test_energy_noalloc_rejects_oversized_grid():
