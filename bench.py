@@ -292,6 +292,7 @@ def run_grace(args, rank, world, local):
     import torch
 
     import workloads
+    from paper_1411_2565_gb300 import _lib
     from paper_1411_2565_gb300 import build as libbuild
     from paper_1411_2565_gb300.grace import Grace
 
@@ -303,7 +304,8 @@ def run_grace(args, rank, world, local):
     libbuild.build()
     w = getattr(workloads, args.workload)()
     f, m0 = w.films[0], w.m0[0]
-    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=dev)
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=dev)   # tuned schedule
+    options = g.options
     g.set_hext(f.hext)
     m_dev = torch.from_numpy(m0.reshape(-1)).to(dev)
     g.set_m(m_dev)
@@ -443,7 +445,10 @@ def run_grace(args, rank, world, local):
         "config": {"workload": w.name, "cells": ncell, "cell_m": list(f.cell), "dt_s": w.dt,
                    "padded": [int(2 ** math.ceil(math.log2(max(1, 2 * n - 1)))) for n in f.grid],
                    "initial_state": w.note, "l2": "flushed before every timed step (256 MiB write)",
-                   "parallelism": f"replicas x{world}", "wall_s_timed_loop": round(wall, 3)},
+                   "parallelism": f"replicas x{world}", "wall_s_timed_loop": round(wall, 3),
+                   "options": {_lib.OPT_NAMES[k]: v for k, v in sorted(options.items())},
+                   "options_source": "autotuned schedule (local cache, else the shipped GB300 table)"
+                                     if options else "library defaults (no tuned schedule for this shape)"},
         "roofline": roof, "step_roofline": step_roof, "runs_of_5": runs,
         "kernels": kernels, "gpu_launches": launches, "e2e": e2e,
         "cpu_baseline": cpu, "clocks": clk, "workloads": extras,
@@ -496,12 +501,14 @@ def plain_workload_extra(dev, name, flush, steps=200):
     tr = g.trace_read()
     g.trace(0)
     g.close()
+    from paper_1411_2565_gb300 import _lib
+    opts = {_lib.OPT_NAMES[k]: v for k, v in sorted(g.options.items())}
     peak, peak_kind = measured_peaks()
     byt = algorithmic_bytes(g, f)
     step_s = t / steps
     moved = byt["per_cell"] * f.ncells
     return {"workload": w.name, "value": f.ncells * steps / t, "unit": UNIT,
-            "ms_per_step": step_s * 1e3,
+            "ms_per_step": step_s * 1e3, "options": opts,
             "kernels_us": {k: round(v[0] / v[1] * 1e3, 1) for k, v in tr.items()},
             "roofline": kernel_rooflines(tr, byt, peak, peak_kind, name),
             "step_roofline": {
@@ -527,18 +534,32 @@ def extra_workloads(dev, headline):
     for name in ("block", "film_large"):
         if name != headline:
             out[name] = plain_workload_extra(dev, name, flush)
-    # 256-film ensemble, 2000 steps in replayed CUDA graphs (one grouped launch per kernel
-    # and size class per step)
+    # 256-film ensemble, 2000 steps in replayed CUDA graphs: the tuned schedule, and both
+    # batch paths explicitly (grouped launches per size class on side streams; one
+    # persistent cooperative launch per graph)
+    from paper_1411_2565_gb300 import _lib
     w = workloads.ensemble()
+    m_all = torch.from_numpy(np.concatenate([m.reshape(-1) for m in w.m0])).to(dev)
+    ncell = sum(f.ncells for f in w.films)
+    paths = {}
+    for name, opts in (("grouped", {_lib.OPT_PERSISTENT: 0}), ("persistent", {_lib.OPT_PERSISTENT: 1})):
+        gb = GraceBatch(w.films, device=dev, options=opts)
+        gb.set_m(m_all)
+        gb.step(32, w.dt)
+        tp = time_events(lambda: gb.step(2000, w.dt), 1)
+        gb.sync()
+        paths[name] = {"value": ncell * 2000 / tp, "ms_per_step": tp / 2000 * 1e3}
+        gb.close()
     gb = GraceBatch(w.films, device=dev)
-    gb.set_m(torch.from_numpy(np.concatenate([m.reshape(-1) for m in w.m0])).to(dev))
+    gb.set_m(m_all)
     gb.step(32, w.dt)
     t = time_events(lambda: gb.step(2000, w.dt), 1)
-    ncell = sum(f.ncells for f in w.films)
     fused_b = sum(algorithmic_bytes(None, fi)["per_cell"] * fi.ncells for fi in w.films)
     model_b = sum(five_pass_bytes(fi) for fi in w.films)
     step_s = t / 2000
     out["ensemble"] = {"workload": w.name, "films": len(w.films), "cells": ncell,
+                       "options": {_lib.OPT_NAMES[k]: v for k, v in sorted(gb.options.items())},
+                       "paths": paths,
                        "value": ncell * 2000 / t, "unit": UNIT, "ms_per_step": t / 2000 * 1e3,
                        "step_roofline": {
                            "unit": "GB/s", "peak": peak, "peak_source": peak_kind,

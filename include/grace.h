@@ -46,7 +46,10 @@ typedef enum {
                               gamma0 <= 0, dt <= 0, n < 0, unknown option/term bits */
   GRACE_EWORKSPACE = -2,   /* workspace smaller than grace_workspace_size or misaligned */
   GRACE_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
-  GRACE_ETIMEOUT = -4,     /* reserved: a bounded device-side wait expired */
+  GRACE_ETIMEOUT = -4,     /* a bounded device-side wait expired: a grid barrier of the
+                              persistent batch launch (GRACE_OPT_PERSISTENT) waited longer
+                              than GRACE_OPT_BARRIER_TIMEOUT_US; reported by the next
+                              synchronising call (grace_sync, grace_energy, grace_get_m_host) */
   GRACE_ESTATE = -5,       /* call out of order (e.g. step before bind / set_m) */
   GRACE_ENONFINITE = -6,   /* a NaN or Inf appeared in <m> (checked by grace_energy) */
   GRACE_EUNSUPPORTED = -7  /* valid arguments outside what this build supports */
@@ -70,11 +73,27 @@ enum {
                                  before grace_bind only */
   GRACE_OPT_TILE_YZ = 4,      /* kx columns per fused y-z block (0 = automatic); before grace_bind only */
   GRACE_OPT_PDL = 5,          /* 1 (default): consecutive kernels use programmatic dependent launch */
-  GRACE_OPT_INTEGRATOR = 6    /* 0 (default): explicit Euler (Sec. 3); 1: Heun, the explicit
+  GRACE_OPT_INTEGRATOR = 6,   /* 0 (default): explicit Euler (Sec. 3); 1: Heun, the explicit
                                  trapezoid m* = normalise(m + dt f(m)),
                                  m' = normalise(m + dt (f(m) + f(m*))/2), a higher-order
                                  integrator named as future work in Sec. 6 (two H_eff per step;
                                  grace_backward supports Euler only) */
+  GRACE_OPT_TILE_Z = 7,       /* z-pass blocks of films thicker than four cells: 0 (default)
+                                 256 threads, 1 128 threads; before grace_bind only */
+  GRACE_OPT_SIDE_STREAMS = 8, /* batches: 1 (default) the films' launch groups step side by side
+                                 on streams of their own; 0 one after another on the bound stream */
+  GRACE_OPT_PERSISTENT = 9,   /* 1: grace_step takes all films and all steps of a call (of a
+                                 captured graph) in one cooperative launch that walks a work list
+                                 of every group's tiles, with a grid barrier between the y-z and
+                                 the x phase of each step (Euler, constant field, films of at most
+                                 four cells in z with 64 <= Px/2 <= 1024 and 16 <= Py <= 512;
+                                 otherwise, and for traced steps, the grouped launches run).
+                                 0 (default): grouped launches.  Before grace_bind only */
+  GRACE_OPT_BARRIER_TIMEOUT_US = 10, /* bound of each grid-barrier wait of the persistent launch,
+                                 microseconds (1e3..6e7, default 1e6) */
+  GRACE_OPT_TEST_SKIP_ARRIVE = 11 /* failure-detection test hook: block `value` of the persistent
+                                 launch skips its first barrier arrival, so every wait runs out
+                                 and the launch ends with GRACE_ETIMEOUT; -1 (default) off */
 };
 
 /* Kernel kinds reported by grace_trace_read. */
@@ -189,6 +208,11 @@ int grace_heff(grace_ctx *ctx, float *dev_h, unsigned term_mask);
  * stream.  Advances the handle's time by n dt_s. */
 int grace_step(grace_ctx *ctx, int n, double dt_s);
 
+/* grace_sync - synchronise the bound stream; GRACE_ETIMEOUT if a persistent launch since the
+ * last report had a grid barrier time out (the state is then that of the last completed
+ * step phase; the barrier words are cleared, so later steps run again). */
+int grace_sync(grace_ctx *ctx);
+
 /*
  * grace_energy - FP64 energies of the current state (Eq. 1 times the cell volume):
  * out[0..4] = {E_exch, E_anis, E_demag, E_zeeman, E_total}, summed over all films, and
@@ -257,6 +281,17 @@ int grace_trace_read(grace_ctx *ctx, double ms[8], long long counts[8]);
 int grace_energy_noalloc(const int grid[3], const double cell_m[3], double Ms, double A, double Ku,
                          const double hext[3], const float *dev_m, const float *dev_hdemag,
                          void *cuda_stream, double out[5], double mavg[3]);
+
+/*
+ * grace_debug_check - checked builds (libgrace_debug.so, built with -DGRACE_DEBUG): the kernels
+ * record failed device-side checks in a word of the workspace instead of trapping (1: a
+ * spectrum index outside its film, 2: a cell index outside its film, 4: a shared-memory
+ * layout larger than the launch provided, 8: a tensor index outside its slots), and every
+ * runtime buffer of the workspace is followed by a 256-byte guard region written at bind.
+ * Synchronises the stream, stores in *flags the OR of the recorded bits and 32 if a guard
+ * region was overwritten, then clears the word.  Release builds: GRACE_EUNSUPPORTED.
+ */
+int grace_debug_check(grace_ctx *ctx, unsigned *flags);
 
 /* grace_set_option - see GRACE_OPT_*. */
 int grace_set_option(grace_ctx *ctx, int option, long long value);

@@ -5,7 +5,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgrace.so")
+# GRACE_DEBUG=1 selects the checked build (device-side index checks, workspace guards)
+DEBUG = os.environ.get("GRACE_DEBUG", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libgrace_debug.so" if DEBUG else "libgrace.so")
 
 GRACE_OK = 0
 STATUS = {0: "GRACE_OK", -1: "GRACE_EINVAL", -2: "GRACE_EWORKSPACE", -3: "GRACE_ECUDA",
@@ -13,6 +15,12 @@ STATUS = {0: "GRACE_OK", -1: "GRACE_EINVAL", -2: "GRACE_EWORKSPACE", -3: "GRACE_
           -7: "GRACE_EUNSUPPORTED"}
 TERM_DEMAG, TERM_EXCH, TERM_ANIS, TERM_ZEEMAN, TERM_ALL = 1, 2, 4, 8, 15
 OPT_GRAPH, OPT_GRAPH_STEPS, OPT_TILE_X, OPT_TILE_YZ, OPT_PDL, OPT_INTEGRATOR = 1, 2, 3, 4, 5, 6
+OPT_TILE_Z, OPT_SIDE_STREAMS = 7, 8
+OPT_PERSISTENT, OPT_BARRIER_TIMEOUT_US, OPT_TEST_SKIP_ARRIVE = 9, 10, 11
+OPT_NAMES = {OPT_GRAPH: "graph", OPT_GRAPH_STEPS: "graph_steps", OPT_TILE_X: "tile_x",
+             OPT_TILE_YZ: "tile_yz", OPT_PDL: "pdl", OPT_INTEGRATOR: "integrator", OPT_TILE_Z: "tile_z",
+             OPT_SIDE_STREAMS: "side_streams", OPT_PERSISTENT: "persistent",
+             OPT_BARRIER_TIMEOUT_US: "barrier_timeout_us", OPT_TEST_SKIP_ARRIVE: "test_skip_arrive"}
 KERNEL_NAMES = ("yz_fast", "x_fast", "yz", "y", "z", "x", "y_fast", "z_fast")
 
 _P = C.c_void_p
@@ -29,6 +37,8 @@ SIGNATURES = {
     "grace_ncells": (_I, [_P, C.POINTER(C.c_longlong)]),
     "grace_bind": (_I, [_P, _P, _SZ, _P]),
     "grace_set_m": (_I, [_P, _P]),
+    "grace_sync": (_I, [_P]),
+    "grace_debug_check": (_I, [_P, C.POINTER(C.c_uint)]),
     "grace_get_m": (_I, [_P, _P]),
     "grace_set_m_host": (_I, [_P, _P]),
     "grace_get_m_host": (_I, [_P, _P]),
@@ -62,8 +72,8 @@ def load(path: str = LIB_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise RuntimeError(f"{path} is missing: build it with paper_1411_2565_gb300.build.build() "
-                           "(there is no CPU fallback)")
+        raise RuntimeError(f"{path} is missing: build it with paper_1411_2565_gb300.build.build("
+                           f"debug={DEBUG}) (there is no CPU fallback)")
     lib = C.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)

@@ -1,10 +1,20 @@
 """Autotuner for the launch schedule of a film or an ensemble.
 
-For a given set of films it times each candidate schedule — x-pass tile (one line per
-block or the larger compiled tile), kx columns per fused y block, steps per captured CUDA
-graph and programmatic dependent launch — on the real device with CUDA events and keeps
-the fastest.  Results are cached in a JSON file keyed by the film shapes and the device
-name, so a later ``Grace(..., options=autotune.best(...))`` reuses them without timing.
+For a given set of films it times each candidate schedule on the real device with CUDA
+events and keeps the fastest.  The candidates are the FFT tiles (x-pass lines per block:
+one line or the larger compiled tile; kx columns per fused y block; z-pass blocks of 256
+or 128 threads, i.e. 16 or 8 columns of a 128-point transform), the batch grouping (the
+launch groups of an ensemble stepping side by side on streams of their own, one after
+another, or all in one persistent cooperative launch) and the steps per captured CUDA graph.
+Options that cannot affect the films (a z tile for films without an FFT along z, side
+streams for one film) keep their defaults instead of multiplying the search; programmatic
+dependent launch stays on (captured graphs, which the timings replay, do not use it, and
+for single-step calls it measured faster).
+
+Results are cached in a JSON file keyed by the film shapes and the device name.
+``Grace`` and ``GraceBatch`` apply ``best()`` by default — the local cache, else the table
+shipped with the package (``tuned_gb300.json``, written by ``python -m
+paper_1411_2565_gb300.autotune``), else the library's own heuristics.
 """
 from __future__ import annotations
 
@@ -27,10 +37,25 @@ SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.
 CANDIDATES = {
     _lib.OPT_TILE_X: (0, 1, 2),
     _lib.OPT_TILE_YZ: (0, 1, 2, 4),
+    _lib.OPT_TILE_Z: (0, 1),
+    _lib.OPT_SIDE_STREAMS: (1, 0),
+    _lib.OPT_PERSISTENT: (0, 1),
     _lib.OPT_GRAPH_STEPS: (8, 16, 32),
     _lib.OPT_PDL: (0, 1),
 }
-BIND_OPTIONS = (_lib.OPT_TILE_X, _lib.OPT_TILE_YZ)
+DEFAULTS = {_lib.OPT_TILE_X: 0, _lib.OPT_TILE_YZ: 0, _lib.OPT_TILE_Z: 0, _lib.OPT_SIDE_STREAMS: 1,
+            _lib.OPT_PERSISTENT: 0, _lib.OPT_GRAPH_STEPS: 16, _lib.OPT_PDL: 1}
+BIND_OPTIONS = (_lib.OPT_TILE_X, _lib.OPT_TILE_YZ, _lib.OPT_TILE_Z, _lib.OPT_PERSISTENT)
+
+
+def relevant(films) -> Dict[int, bool]:
+    """Which options can change how these films run (the rest keep DEFAULTS)."""
+    thin = any(f.grid[2] <= 4 for f in films)
+    thick = any(f.grid[2] > 4 for f in films)
+    batch = len(films) > 1
+    return {_lib.OPT_TILE_X: True, _lib.OPT_TILE_YZ: thin, _lib.OPT_TILE_Z: thick,
+            _lib.OPT_SIDE_STREAMS: batch, _lib.OPT_PERSISTENT: batch and thin and not thick,
+            _lib.OPT_GRAPH_STEPS: True, _lib.OPT_PDL: False}
 
 
 def _key(films, device) -> str:
@@ -88,8 +113,9 @@ def tune(films: Sequence, m0s: Sequence[np.ndarray], dt: float, device="cuda", f
     if key in cache and not force:
         return {int(k): v for k, v in cache[key]["options"].items()}
     results = []
+    use = relevant(films)
     names = list(CANDIDATES)
-    for values in itertools.product(*(CANDIDATES[n] for n in names)):
+    for values in itertools.product(*(CANDIDATES[n] if use[n] else (DEFAULTS[n],) for n in names)):
         opts = dict(zip(names, values))
         try:
             ms = _time(films, m0s, dt, opts, device)
@@ -105,10 +131,49 @@ def tune(films: Sequence, m0s: Sequence[np.ndarray], dt: float, device="cuda", f
 
 
 def best(films: Sequence, device="cuda") -> Dict[int, int]:
-    """Cached options for these films: the local cache, else the shipped GB300 table, else {}."""
+    """Cached options for these films: the local cache, else the shipped GB300 table, else {}.
+    An entry that predates an option gets that option's default."""
     key = _key(films, torch.device(device))
     entry = _load().get(key)
     if entry is None and os.path.exists(SHIPPED):
         with open(SHIPPED) as fh:
             entry = json.load(fh).get(key)
-    return {} if entry is None else {int(k): v for k, v in entry["options"].items()}
+    if entry is None:
+        return {}
+    opts = dict(DEFAULTS)
+    opts.update({int(k): v for k, v in entry["options"].items()})
+    return opts
+
+
+def main(argv=None):
+    """Tune the benchmark workloads on this device and write the table ``best`` ships with."""
+    import argparse
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import workloads
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--workloads", default="block,film_large,film_small,ensemble,adjoint_film")
+    ap.add_argument("--out", default=SHIPPED)
+    args = ap.parse_args(argv)
+    table = {}
+    if os.path.exists(args.out):
+        with open(args.out) as fh:
+            table = json.load(fh)
+    for name in args.workloads.split(","):
+        w = getattr(workloads, name)()
+        opts = tune(w.films, w.m0, w.dt, force=True)
+        key = _key(w.films, torch.device("cuda"))
+        entry = _load()[key]
+        entry["workload"] = w.name
+        table[key] = entry
+        print(name, {k: v for k, v in opts.items()}, f"{entry['ms_per_step']:.4f} ms/step", flush=True)
+    tmp = args.out + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(table, fh, indent=1)
+    os.replace(tmp, args.out)
+
+
+if __name__ == "__main__":
+    main()

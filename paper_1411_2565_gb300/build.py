@@ -3,6 +3,8 @@
 Each translation unit is compiled by nvcc in parallel, then linked as a shared
 library next to this file.  Objects go to ``_build/`` beside the package (ignored
 by git).  A rebuild happens only when a source or header is newer than the library.
+``build(debug=True)`` makes the checked variant ``libgrace_debug.so`` (-DGRACE_DEBUG:
+device-side index checks and workspace guard regions; loaded when GRACE_DEBUG=1).
 """
 from __future__ import annotations
 
@@ -18,8 +20,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrace.so")
+LIB_DEBUG = os.path.join(HERE, "libgrace_debug.so")
 SOURCES = ["fastx_q1024.cu", "fastx_q512.cu", "fastx_q128.cu", "fastx_q8.cu", "fastyz.cu", "fastsplit.cu",
-           "api.cu", "hotpath.cu", "tensor.cu", "fastx.cu", "noalloc.cu"]
+           "api.cu", "hotpath.cu", "tensor.cu", "fastx.cu", "noalloc.cu", "persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -37,23 +40,26 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libgrace.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile and link libgrace.so (debug: libgrace_debug.so); returns its path."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and up_to_date(lib):
+        return lib
+    out = os.path.join(BUILD, "debug") if debug else BUILD
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
+    flags = FLAGS + (["-DGRACE_DEBUG"] if debug else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out, os.path.splitext(src)[0] + ".o")
+        cmd = [cc, *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -63,14 +69,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     r = subprocess.run([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -13,7 +13,9 @@
 
 #include "fft.cuh"
 #include "grace.h"
+#include "debug.cuh"
 #include "internal.cuh"
+#include "persist.cuh"
 
 using namespace grace;
 
@@ -48,6 +50,13 @@ constexpr size_t kSmemMax = 200 * 1024;
 constexpr int kThreadsHost = 256;
 constexpr int kTaskCap = 8 * 4 * kThreadsHost;  // points per block the FFT helper can hold
 constexpr int kEnergyBlocks = 304;
+#ifdef GRACE_DEBUG
+constexpr bool kChecked = true;     // libgrace_debug.so: device-side checks and workspace guards
+#else
+constexpr bool kChecked = false;
+#endif
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
 
 }  // namespace
 
@@ -61,6 +70,7 @@ struct Group {
   bool fused = true;
   int Q = 0, Py = 0, nz = 0, Pz = 0;
   int TY = 1, KPB = 1, RPB = 1, TQ = 1;
+  int ZT = 256;             // threads per z-pass block (split path): 256 or 128
   bool xhelp = false;       // x pass with helper warps (few blocks in flight)
   int units[UK_COUNT] = {0, 0, 0, 0, 0};
   size_t smem_x = 0, smem_yz = 0, smem_y = 0, smem_z = 0;
@@ -78,6 +88,17 @@ struct grace_ctx {
   std::vector<int> film_group;
   long long ncell = 0;
   int tile_x = 0, tile_yz = 0;      // 0 = automatic
+  int tile_z = 0;                   // z-pass blocks: 0 = 256 threads, 1 = 128 threads
+  bool side_streams = true;         // batch groups step side by side on streams of their own
+  bool persist = false;             // GRACE_OPT_PERSISTENT: one cooperative launch for all groups
+  bool persist_ok = false;          // ... and every group has a persistent tile body
+  int persist_grid = 0;             // co-resident blocks of the persistent kernel
+  size_t persist_smem = 0;
+  int skip_arrive = -1;             // test hook: block that skips its first barrier arrival
+  long long barrier_timeout_us = 1000000;
+  size_t o_psync = 0, o_pgroups = 0;
+  size_t o_dbg = 0;                 // checked builds: the device-side check word
+  std::vector<size_t> guards;       // checked builds: guard regions after runtime buffers
   size_t o_tw = 0, o_films = 0, o_run = 0, o_m0 = 0, o_m1 = 0, o_H = 0, o_k1 = 0, o_part = 0, o_eout = 0;
   size_t o_time = 0;                // device time (double) and envelope scale {s(t), s(t + dt)}
   std::vector<size_t> o_S;
@@ -209,11 +230,14 @@ int plan_group(grace_ctx* c, Group& g) {
     g.xhelp = pick_x_help();
     g.smem_x = fast_x_smem(g.Q, g.TY);
     g.RPB = fast_y_rows(g.Py);
-    g.TQ = fast_z_cols(g.Pz);
+    g.ZT = c->tile_z == 1 ? 128 : 256;
+    g.TQ = fast_z_cols(g.Pz, g.ZT);
     if (g.smem_x > kSmemMax) return GRACE_EUNSUPPORTED;
   } else if (g.fast) {
     g.fused = true;
-    g.TY = pick_x_tile();      // one of the two compile-time tiles of the fast x pass
+    // one of the two compile-time tiles of the fast x pass (the persistent kernel's bodies
+    // take the large one)
+    g.TY = c->persist ? fast_x_tile(g.Q) : pick_x_tile();
     g.xhelp = pick_x_help();
     g.smem_x = fast_x_smem(g.Q, g.TY);
     const int per = g.nz * (g.Py / 8);
@@ -221,6 +245,17 @@ int plan_group(grace_ctx* c, Group& g) {
     while (KPB > 1 && KPB * per > 256) --KPB;
     if (c->tile_yz <= 0)
       while (KPB > 1 && yzunits(KPB) < want) KPB /= 2;
+    if (c->persist) {
+      // the persistent kernel's 256-thread blocks: a tile's row threads must be whole warps
+      // (the rest only keep step with the transforms' barriers, which are warp-aligned)
+      KPB = 0;
+      for (int k = 256 / per; k >= 1; --k)
+        if ((k * per) % 32 == 0) {
+          KPB = k;
+          break;
+        }
+      if (KPB == 0) KPB = 1;   // no whole-warp tile: persist_ok rejects the group below
+    }
     g.KPB = KPB;
     g.smem_yz = fast_yz_smem(g.Py, g.nz, KPB);
     if (g.smem_x > kSmemMax || g.smem_yz > kSmemMax) return GRACE_EUNSUPPORTED;
@@ -398,33 +433,55 @@ int plan(grace_ctx* c) {
     g.o_desc = o;
     o = al256(o + g.idx.size() * sizeof(FilmDev));
   }
+  c->o_psync = o;
+  o = al256(o + sizeof(PersistSync));
+  c->o_dbg = o;
+  o = al256(o + (kChecked ? sizeof(unsigned) : 0));
+  c->o_pgroups = o;
+  o = al256(o + c->groups.size() * sizeof(PersistGroup));
   for (auto& s : c->classes) {
     s.t_off = o;
     o = al256(o + (size_t)s.Kx * s.nslot * s.Ky * sizeof(float));
   }
   c->o_run = o;
   size_t r = 0;
+  c->guards.clear();
+  // checked builds: a guard region after every runtime buffer (offsets within the runtime area)
+  auto guard = [&]() {
+    if (kChecked) {
+      c->guards.push_back(r);
+      r += kGuardBytes;
+    }
+  };
   c->o_S.assign(c->films.size(), 0);
   for (size_t i = 0; i < c->films.size(); ++i) {
     const FilmDev& d = c->fd[i];
     c->o_S[i] = r;
     r = al256(r + (size_t)3 * d.nz * d.Kx * d.srow * sizeof(float2));
+    guard();
   }
   const size_t mbytes = al256((size_t)3 * c->ncell * sizeof(float));
   c->o_m0 = r;
   r += mbytes;
+  guard();
   c->o_m1 = r;
   r += mbytes;
+  guard();
   c->o_H = r;
   r += mbytes;
+  guard();
   c->o_k1 = r;
   r += mbytes;
+  guard();
   c->o_part = r;
   r = al256(r + (size_t)kEnergyBlocks * 8 * sizeof(double));
+  guard();
   c->o_eout = r;
   r = al256(r + 8 * sizeof(double));
+  guard();
   c->o_time = r;
   r = al256(r + 2 * sizeof(double));
+  guard();
   c->run_bytes = r;
   size_t b = 0;
   for (auto& s : c->classes) {
@@ -437,6 +494,18 @@ int plan(grace_ctx* c) {
   }
   c->build_bytes = b;
   c->need = c->o_run + std::max(c->run_bytes, c->build_bytes);
+  // the persistent launch needs a compiled tile body for every group (fused path, large x tile)
+  c->persist_ok = c->persist;
+  c->persist_smem = 0;
+  for (const auto& g : c->groups) {
+    // tiles on 256-thread blocks whose transforming threads are whole warps (the others
+    // only execute the transforms' block barriers, which must not split a warp)
+    const bool ok = g.fast && !g.split_fast && persist_x_kind(g.Q) >= 0 && persist_yz_kind(g.Py, g.nz) >= 0 &&
+                    g.TY == fast_x_tile(g.Q) && (g.TY * g.Q / 8) % 32 == 0 &&
+                    (g.KPB * g.nz * (g.Py / 8)) % 32 == 0 && g.KPB * g.nz * (g.Py / 8) <= kPersistThreads;
+    c->persist_ok = c->persist_ok && ok;
+    c->persist_smem = std::max(c->persist_smem, std::max(g.smem_x, g.smem_yz));
+  }
   return GRACE_OK;
 }
 
@@ -450,6 +519,7 @@ void fill_pointers(grace_ctx* c) {
     d.T = reinterpret_cast<const float*>(c->ws + s.t_off);
     d.ms_field = c->ms_field ? c->ms_field + d.cell0 : nullptr;
     d.h_field = c->h_field ? c->h_field + 3 * d.cell0 : nullptr;
+    d.dbg = kChecked ? reinterpret_cast<unsigned*>(c->ws + c->o_dbg) : nullptr;
   }
   for (auto& g : c->groups) {
     g.fd.clear();
@@ -521,7 +591,7 @@ cudaError_t enqueue_conv(grace_ctx* c, const Group& g, const LaunchP& lp, cudaSt
   const FilmDev* f = gfilms(c, g);
   if (g.split_fast) {
     GRACE_LAUNCH(c, TK_Y_FAST, s, launch_fast_y(g.Py, -1, f, lp, g.units[UK_Y], s));
-    GRACE_LAUNCH(c, TK_Z_FAST, s, launch_fast_z(g.Pz, f, lp, g.units[UK_Z], s));
+    GRACE_LAUNCH(c, TK_Z_FAST, s, launch_fast_z(g.Pz, g.ZT, f, lp, g.units[UK_Z], s));
     GRACE_LAUNCH(c, TK_Y_FAST, s, launch_fast_y(g.Py, +1, f, lp, g.units[UK_Y], s));
     return cudaSuccess;
   }
@@ -589,10 +659,33 @@ int parity_flip(const grace_ctx* c);
 // with several groups and no envelope each group takes its n steps on a stream of its
 // own (forked from s and joined back into it): small groups run beside large ones, and a
 // captured graph holds one branch per group.
+bool use_persist(const grace_ctx* c) { return c->persist_ok && !c->pulse && c->integrator == 0 && !c->trace; }
+
+PersistSync* persist_sync(const grace_ctx* c) { return reinterpret_cast<PersistSync*>(c->ws + c->o_psync); }
+
 cudaError_t enqueue_steps(grace_ctx* c, int n, int parity, float dt, double ddt, cudaStream_t s) {
+  if (use_persist(c)) {
+    // every group, all n steps: one cooperative launch walking the work list
+    PersistArgs a{};
+    a.groups = reinterpret_cast<const PersistGroup*>(c->ws + c->o_pgroups);
+    a.ngroups = (int)c->groups.size();
+    for (const auto& g : c->groups) {
+      a.total_yz += g.units[UK_YZ];
+      a.total_x += g.units[UK_X];
+    }
+    a.nsteps = n;
+    a.parity0 = parity;
+    a.sync = persist_sync(c);
+    a.skip_arrive_block = c->skip_arrive;
+    a.limit_ns = (unsigned long long)c->barrier_timeout_us * 1000ull;
+    a.lp = group_lp(c, c->groups[0]);
+    a.lp.dt = dt;
+    a.lp.pdl = 0;
+    return persist_launch(a, c->persist_grid, c->persist_smem, s);
+  }
   const int flip = parity_flip(c);
   const size_t ng = c->groups.size();
-  if (ng < 2 || c->pulse) {
+  if (ng < 2 || c->pulse || !c->side_streams) {
     for (int k = 0; k < n; ++k) {
       cudaError_t e = enqueue_step(c, (parity + k * flip) & 1, dt, ddt, s);
       if (e != cudaSuccess) return e;
@@ -686,6 +779,19 @@ void drop_graphs(grace_ctx* c) {
     if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
     c->gexec[p] = nullptr;
   }
+}
+
+// After a stream synchronisation: a persistent launch whose grid barrier timed out left
+// GRACE_ETIMEOUT in the status word; report it once and clear the barrier words.
+int persist_status(grace_ctx* c) {
+  if (!c->persist_ok) return GRACE_OK;
+  PersistSync h{};
+  GRACE_CUDA(c, cudaMemcpy(&h, c->ws + c->o_psync, sizeof h, cudaMemcpyDeviceToHost));
+  if (h.status == 0) return GRACE_OK;
+  GRACE_CUDA(c, cudaMemsetAsync(c->ws + c->o_psync, 0, sizeof(PersistSync), c->stream));
+  GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
+  return fail(c, GRACE_ETIMEOUT, "a grid barrier of the persistent batch launch timed out; the steps "
+                                 "after it were not taken");
 }
 
 int ready(grace_ctx* c, bool need_m) {
@@ -828,6 +934,41 @@ int grace_bind(grace_ctx* c, void* dev_ws, size_t bytes, void* cuda_stream) {
   fill_pointers(c);
   int st = upload_films(c);
   if (st != GRACE_OK) return st;
+  if (c->persist_ok) {
+    // the persistent kernel's work list (groups in order, tiles numbered across groups),
+    // its barrier words cleared, and its grid: every block co-resident
+    int bps = 0;
+    GRACE_CUDA(c, persist_configure(std::max<size_t>(c->persist_smem, 1), &bps));
+    c->persist_grid = bps * sm_count();
+    if (c->persist_grid < 1) {
+      c->persist_ok = false;
+    } else {
+      std::vector<PersistGroup> pg;
+      int fy = 0, fx = 0;
+      for (const auto& g : c->groups) {
+        PersistGroup e{};
+        e.films = gfilms(c, g);
+        e.nfilms = (int)g.idx.size();
+        e.kind_yz = persist_yz_kind(g.Py, g.nz);
+        e.kind_x = persist_x_kind(g.Q);
+        e.kpb = g.KPB;
+        e.first_yz = fy;
+        e.first_x = fx;
+        fy += g.units[UK_YZ];
+        fx += g.units[UK_X];
+        pg.push_back(e);
+      }
+      GRACE_CUDA(c, cudaMemcpyAsync(c->ws + c->o_pgroups, pg.data(), pg.size() * sizeof(PersistGroup),
+                                    cudaMemcpyHostToDevice, c->stream));
+      GRACE_CUDA(c, cudaMemsetAsync(c->ws + c->o_psync, 0, sizeof(PersistSync), c->stream));
+    }
+  }
+  if (kChecked) {
+    // the tensor build used the runtime area as scratch: the guards are written after it
+    for (size_t g : c->guards)
+      GRACE_CUDA(c, cudaMemsetAsync(c->ws + c->o_run + g, kGuardByte, kGuardBytes, c->stream));
+    GRACE_CUDA(c, cudaMemsetAsync(c->ws + c->o_dbg, 0, sizeof(unsigned), c->stream));
+  }
   GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
   GRACE_CUDA(c, launch_set_time(dev_time(c), c->t, c->stream));
   GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -879,7 +1020,35 @@ int grace_get_m_host(grace_ctx* c, float* host_m) {
   GRACE_CUDA(c, cudaMemcpyAsync(host_m, src, (size_t)3 * c->ncell * sizeof(float),
                                 cudaMemcpyDeviceToHost, c->stream));
   GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
+  return persist_status(c);
+}
+
+int grace_debug_check(grace_ctx* c, unsigned* flags) {
+  if (!c || !flags) return GRACE_EINVAL;
+  *flags = 0;
+  if (!kChecked) return fail(c, GRACE_EUNSUPPORTED, "not a checked build (libgrace_debug.so has the checks)");
+  int st = ready(c, false);
+  if (st) return st;
+  GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
+  unsigned word = 0;
+  GRACE_CUDA(c, cudaMemcpy(&word, c->ws + c->o_dbg, sizeof word, cudaMemcpyDeviceToHost));
+  std::vector<unsigned char> h(kGuardBytes);
+  for (size_t g : c->guards) {
+    GRACE_CUDA(c, cudaMemcpy(h.data(), c->ws + c->o_run + g, kGuardBytes, cudaMemcpyDeviceToHost));
+    for (unsigned char b : h)
+      if (b != kGuardByte) word |= DBG_GUARD;
+  }
+  *flags = word;
+  GRACE_CUDA(c, cudaMemsetAsync(c->ws + c->o_dbg, 0, sizeof(unsigned), c->stream));
+  GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
   return GRACE_OK;
+}
+
+int grace_sync(grace_ctx* c) {
+  int st = ready(c, false);
+  if (st) return st;
+  GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
+  return persist_status(c);
 }
 
 int grace_get_m_host_async(grace_ctx* c, float* host_m) {
@@ -1036,6 +1205,7 @@ int grace_energy(grace_ctx* c, double out[5], double mavg[3]) {
   double h[8];
   GRACE_CUDA(c, cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, c->stream));
   GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
+  if ((st = persist_status(c))) return st;
   if (out) {
     for (int k = 0; k < 4; ++k) out[k] = h[k];
     out[4] = h[0] + h[1] + h[2] + h[3];
@@ -1104,51 +1274,127 @@ int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt
   float* nu = state(nck + segn + 3);
   const bool saved_trace = c->trace;
   c->trace = false;
+  const size_t sf = sb / sizeof(float);
+
+  // Runs of kernels and copies go through CUDA graphs, captured once per distinct run and
+  // replayed (a small film's step is a few microseconds of work per launch): the `ckpt`
+  // forward steps between checkpoints, and per segment the recompute of its states plus
+  // its backward steps.  A run's graph depends only on the m buffer it starts from and on
+  // which of the two lambda buffers holds lambda_{k+1}; everything that differs between
+  // segments (the checkpoint copied in) stays outside it.  Without graphs (GRACE_OPT_GRAPH
+  // = 0) the same runs are launched directly.
+  struct Run {
+    int kind, len, parity;
+    const float* lam;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Run> runs;
+  auto cleanup = [&]() {
+    for (auto& r : runs)
+      if (r.exec) cudaGraphExecDestroy(r.exec);
+    runs.clear();
+    c->trace = saved_trace;
+  };
+  const bool graphs = c->use_graph && c->cap;
+  auto run = [&](int kind, int len, const float* lam, auto&& body) -> int {
+    if (!graphs) {
+      GRACE_CUDA(c, body(c->stream));
+      return GRACE_OK;
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto& r : runs)
+      if (r.kind == kind && r.len == len && r.parity == c->parity && r.lam == lam) exec = r.exec;
+    if (!exec) {
+      const bool pdl = c->pdl;
+      c->pdl = false;   // inside a graph plain serialisation measured faster than programmatic edges
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        e = body(c->cap);
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+        if (e == cudaSuccess) e = e2;
+      }
+      c->pdl = pdl;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "backward graph capture");
+      runs.push_back({kind, len, c->parity, lam, exec});
+    }
+    GRACE_CUDA(c, cudaGraphLaunch(exec, c->stream));
+    return GRACE_OK;
+  };
 
   // forward from m_0, keeping the state at every checkpoint
-  if ((st = copy_state(c, ck0, cur_m(c)))) return st;
+  if ((st = copy_state(c, ck0, cur_m(c)))) return cleanup(), st;
   for (int s = 1; s < nck; ++s) {
-    for (int k = 0; k < ckpt; ++k) {
-      GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, dt, c->stream));
-      c->parity ^= 1;
-    }
-    if ((st = copy_state(c, state(s), cur_m(c)))) return st;
+    const int p0 = c->parity;
+    st = run(0, ckpt, nullptr, [&](cudaStream_t sm) {
+      for (int k = 0; k < ckpt; ++k) {
+        const cudaError_t e = enqueue_step(c, (p0 + k) & 1, fdt, dt, sm);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    });
+    if (st) return cleanup(), st;
+    c->parity = (p0 + ckpt) & 1;
+    if ((st = copy_state(c, state(s), cur_m(c)))) return cleanup(), st;
   }
-  if ((st = copy_state(c, lamA, dL_dmT))) return st;
+  if ((st = copy_state(c, lamA, dL_dmT))) return cleanup(), st;
   for (int s = nck - 1; s >= 0 && n > 0; --s) {
     const int k0 = s * ckpt;
     const int len = std::min(ckpt, n - k0);
-    // recompute the segment's states m_{k0} .. m_{k0+len-1}
-    if ((st = copy_state(c, cur_m(c), state(s)))) return st;
-    GRACE_CUDA(c, enqueue_r2c(c));
-    for (int j = 0; j < len; ++j) {
-      if ((st = copy_state(c, seg0 + (size_t)j * (sb / sizeof(float)), cur_m(c)))) return st;
-      if (j + 1 < len) {
-        GRACE_CUDA(c, enqueue_step(c, c->parity, fdt, dt, c->stream));
-        c->parity ^= 1;
+    // the segment's checkpoint m_{k0} and its spectrum
+    if ((st = copy_state(c, cur_m(c), state(s)))) return cleanup(), st;
+    const cudaError_t er = enqueue_r2c(c);
+    if (er != cudaSuccess) return cleanup(), cuda_fail(c, er, "R2C launch");
+    const int p0 = c->parity;
+    float* la = lamA;
+    float* lb = lamB;
+    st = run(1, len, lamA, [&](cudaStream_t sm) {
+      // recompute m_{k0} .. m_{k0+len-1} into the segment buffer
+      int p = p0;
+      auto mbuf = [&](int par) {
+        return reinterpret_cast<float*>(c->ws + c->o_run + (par ? c->o_m1 : c->o_m0));
+      };
+      for (int j = 0; j < len; ++j) {
+        cudaError_t e = cudaMemcpyAsync(seg0 + (size_t)j * sf, mbuf(p), (size_t)3 * c->ncell * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, sm);
+        if (e == cudaSuccess && j + 1 < len) {
+          e = enqueue_step(c, p, fdt, dt, sm);
+          p ^= 1;
+        }
+        if (e != cudaSuccess) return e;
       }
-    }
-    for (int j = len - 1; j >= 0; --j) {
-      const float* mk = seg0 + (size_t)j * (sb / sizeof(float));
-      for (const auto& g : c->groups) {
-        LaunchP lp = group_lp(c, g);
-        lp.dt = fdt;
-        lp.mk = mk;
-        lp.adj_lam_in = lamA;
-        lp.adj_lam_part = lampart;
-        lp.adj_nu = nu;
-        lp.adj_lam_out = lamB;
-        lp.adj_g_hext = g_hext;
-        lp.adj_g_ms = g_ms;
-        GRACE_CUDA(c, enqueue_x(c, g, XM_R2C, lp, c->stream));
-        GRACE_CUDA(c, enqueue_conv(c, g, lp, c->stream));
-        GRACE_CUDA(c, enqueue_x(c, g, XM_ADJ1, lp, c->stream));
-        GRACE_CUDA(c, enqueue_conv(c, g, lp, c->stream));
-        GRACE_CUDA(c, enqueue_x(c, g, XM_ADJ2, lp, c->stream));
+      // backward through the segment: lambda_{k+1} -> lambda_k
+      float* li = la;
+      float* lo = lb;
+      for (int j = len - 1; j >= 0; --j) {
+        for (const auto& g : c->groups) {
+          LaunchP lp = group_lp(c, g);
+          lp.dt = fdt;
+          lp.mk = seg0 + (size_t)j * sf;
+          lp.adj_lam_in = li;
+          lp.adj_lam_part = lampart;
+          lp.adj_nu = nu;
+          lp.adj_lam_out = lo;
+          lp.adj_g_hext = g_hext;
+          lp.adj_g_ms = g_ms;
+          cudaError_t e = enqueue_x(c, g, XM_R2C, lp, sm);
+          if (e == cudaSuccess) e = enqueue_conv(c, g, lp, sm);
+          if (e == cudaSuccess) e = enqueue_x(c, g, XM_ADJ1, lp, sm);
+          if (e == cudaSuccess) e = enqueue_conv(c, g, lp, sm);
+          if (e == cudaSuccess) e = enqueue_x(c, g, XM_ADJ2, lp, sm);
+          if (e != cudaSuccess) return e;
+        }
+        std::swap(li, lo);
       }
-      std::swap(lamA, lamB);
-    }
+      return cudaSuccess;
+    });
+    if (st) return cleanup(), st;
+    c->parity = (p0 + len - 1) & 1;
+    if (len & 1) std::swap(lamA, lamB);
   }
+  cleanup();
   if (g_m0 && (st = copy_state(c, g_m0, lamA))) return st;
   // leave the state at m_0
   if ((st = copy_state(c, cur_m(c), ck0))) return st;
@@ -1178,20 +1424,46 @@ int grace_set_option(grace_ctx* c, int option, long long value) {
       drop_graphs(c);
       return GRACE_OK;
     case GRACE_OPT_TILE_X:
-    case GRACE_OPT_TILE_YZ: {
+    case GRACE_OPT_TILE_YZ:
+    case GRACE_OPT_TILE_Z: {
       if (c->bound) return fail(c, GRACE_ESTATE, "tile options must be set before grace_bind");
       if (value < 0 || value > 64) return fail(c, GRACE_EINVAL, "tile option out of range 0..64");
-      const int old_x = c->tile_x, old_yz = c->tile_yz;
-      (option == GRACE_OPT_TILE_X ? c->tile_x : c->tile_yz) = (int)value;
+      if (option == GRACE_OPT_TILE_Z && value > 1) return fail(c, GRACE_EINVAL, "GRACE_OPT_TILE_Z takes 0 or 1");
+      const int old_x = c->tile_x, old_yz = c->tile_yz, old_z = c->tile_z;
+      (option == GRACE_OPT_TILE_X ? c->tile_x : option == GRACE_OPT_TILE_YZ ? c->tile_yz : c->tile_z) = (int)value;
       const int st = plan(c);
       if (st != GRACE_OK) {
         c->tile_x = old_x;
         c->tile_yz = old_yz;
+        c->tile_z = old_z;
         plan(c);
         return fail(c, st, "tile option not supported for this shape");
       }
       return GRACE_OK;
     }
+    case GRACE_OPT_SIDE_STREAMS:
+      if (value != 0 && value != 1) return fail(c, GRACE_EINVAL, "GRACE_OPT_SIDE_STREAMS takes 0 or 1");
+      c->side_streams = value != 0;
+      drop_graphs(c);
+      return GRACE_OK;
+    case GRACE_OPT_PERSISTENT: {
+      if (value != 0 && value != 1) return fail(c, GRACE_EINVAL, "GRACE_OPT_PERSISTENT takes 0 or 1");
+      if (c->bound) return fail(c, GRACE_ESTATE, "GRACE_OPT_PERSISTENT must be set before grace_bind");
+      c->persist = value != 0;
+      const int st = plan(c);
+      if (st != GRACE_OK) return fail(c, st, "planning failed");
+      return GRACE_OK;
+    }
+    case GRACE_OPT_BARRIER_TIMEOUT_US:
+      if (value < 1000 || value > 60000000) return fail(c, GRACE_EINVAL, "barrier timeout out of range 1e3..6e7 us");
+      c->barrier_timeout_us = value;
+      drop_graphs(c);
+      return GRACE_OK;
+    case GRACE_OPT_TEST_SKIP_ARRIVE:
+      if (value < -1 || value > 1 << 20) return fail(c, GRACE_EINVAL, "block index out of range");
+      c->skip_arrive = (int)value;
+      drop_graphs(c);
+      return GRACE_OK;
     case GRACE_OPT_GRAPH_STEPS:
       if (value < 2 || value > 4096 || (value & 1)) return fail(c, GRACE_EINVAL, "graph steps: even, 2..4096");
       c->graph_steps = (int)value;

@@ -2,6 +2,7 @@
 // the local terms of H_eff (Eq. 2), the explicit Euler step of Eq. 3 with
 // renormalisation, and the two pointwise halves of its discrete adjoint.
 #pragma once
+#include "debug.cuh"
 #include "internal.cuh"
 
 namespace grace {
@@ -52,6 +53,8 @@ __device__ __forceinline__ CellState cell_field(const FilmDev& f, unsigned mask,
                                                 int i, int x, int y, int z, float hdx, float hdy, float hdz,
                                                 float hs = 1.f) {
   const int N = f.ncell;
+  GRACE_DCHECK(f, i >= 0 && i < N && x >= 0 && x < f.nx && y >= 0 && y < f.ny && z >= 0 && z < f.nz &&
+                      i == (z * f.ny + y) * f.nx + x, DBG_M_INDEX);
   CellState c;
   c.mx = m[i];
   c.my = m[N + i];
@@ -91,6 +94,8 @@ __device__ __forceinline__ void cell_field_pair(const FilmDev& f, unsigned mask,
                                                 int i, int x, int y, int z, float2 hdx, float2 hdy,
                                                 float2 hdz, float hs, CellState& ca, CellState& cb) {
   const int N = f.ncell, nx = f.nx, ny = f.ny, nz = f.nz;
+  GRACE_DCHECK(f, i >= 0 && i + 1 < N && x >= 0 && x + 1 < nx && y >= 0 && y < ny && z >= 0 && z < nz &&
+                      i == (z * ny + y) * nx + x && (i & 1) == 0, DBG_M_INDEX);
   auto ld2 = [&](int k) { return *reinterpret_cast<const float2*>(m + k); };
   const float2 mx = ld2(i), my = ld2(N + i), mz = ld2(2 * N + i);
   ca.mx = mx.x; ca.my = my.x; ca.mz = mz.x;
@@ -195,6 +200,7 @@ __device__ __forceinline__ float3 llg_next(const FilmDev& f, const LaunchP& lp, 
 template <int MODE>
 __device__ __forceinline__ float3 cell_apply(const FilmDev& f, const LaunchP& lp, int i, const CellState& c) {
   const int N = f.ncell;
+  GRACE_DCHECK(f, i >= 0 && i < N, DBG_M_INDEX);
   if (MODE == XM_R2C) return make_float3(c.Ms * c.mx, c.Ms * c.my, c.Ms * c.mz);
   if (MODE == XM_HEFF) {
     float* o = lp.out + 3 * f.cell0;
@@ -284,6 +290,7 @@ struct Adj1In {
 __device__ __forceinline__ Adj1In adj1_load(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
                                             int i, int x, int y, int z) {
   const int N = f.ncell;
+  GRACE_DCHECK(f, i >= 0 && i < N, DBG_M_INDEX);
   Adj1In a;
   a.loc = cell_field(f, 2u | 4u, m, i, x, y, z, 0.f, 0.f, 0.f);
   a.ex = f.hx;
@@ -370,6 +377,7 @@ __device__ __forceinline__ Adj2In adj2_load(const FilmDev& f, const LaunchP& lp,
                                             int i, int x, int y, int z) {
   const int N = f.ncell;
   const long long o = 3 * f.cell0;
+  GRACE_DCHECK(f, i >= 0 && i < N, DBG_M_INDEX);
   Adj2In a;
   a.Ms = cell_ms(f, i);
   const float* nu = lp.adj_nu + o;

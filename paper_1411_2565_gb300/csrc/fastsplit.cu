@@ -1,148 +1,192 @@
 // Split y / z passes with compile-time lengths, for films with nz > 4 (an FFT along z).
 //
-// ky_fast: RPB rows of S per block, Py/8 threads per row; the forward transform reads
-//   the ny rows written by the x pass (zero-padded to Py), the inverse keeps ny outputs.
+// ky_fast: pairs of rows of S, Py/8 threads per pair, the two rows held as a packed lane
+//   pair (fftpk.cuh); the forward transform reads the ny rows written by the x pass
+//   (zero-padded to Py), the inverse keeps ny outputs.
 // kz_fast: TQ columns q = kx * Py + ky per block, Pz/8 threads per column, each thread
-//   holding the 3 components of its column.  After the forward z FFT a thread owns all
-//   three components at kz = j + s Pz/8, so the 6-component real symmetric tensor
-//   product H^ = T . M^ (Sec. 3, with parities: xy odd in ky, xz odd in kz, yz odd in
-//   both) is local to the thread; the inverse z FFT keeps nz outputs.
+//   holding the 3 components of its column: x and y as a packed lane pair, z as a scalar
+//   line (fftpk.cuh).  After the forward z FFT a thread owns all three components at
+//   kz = j + s Pz/8, so the 6-component real symmetric tensor product H^ = T . M^ (Sec. 3,
+//   with parities: xy odd in ky, xz odd in kz, yz odd in both) is local to the thread,
+//   its six tensor values in three 8-byte loads (T[kx][kz][ky][6]); the inverse z FFT
+//   keeps nz outputs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
+#include "debug.cuh"
+#include "fftpk.cuh"
 #include "fftreg.cuh"
 #include "internal.cuh"
 
 namespace grace {
 namespace {
 
+// y pass: RPP pairs of rows per block (128 threads where the row allows, 6 blocks per SM),
+// Py/8 threads per pair, the two rows of a pair as a packed lane pair (fftpk.cuh)
+__host__ __device__ constexpr int y_pairs(int PY) { return 128 / (PY / 8) < 1 ? 1 : 128 / (PY / 8); }
+__host__ __device__ constexpr int y_threads(int PY) { return y_pairs(PY) * (PY / 8); }
+
 template <int PY, int DIR>
-__global__ void __launch_bounds__(256) ky_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+__global__ void __launch_bounds__(y_threads(PY), y_threads(PY) <= 128 ? 6 : 3)
+    ky_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = PY / 8;
-  constexpr int LS = fast_line_stride(PY, T);
-  const int RPB = blockDim.x / T;
+  constexpr int RPP = y_pairs(PY);
+  constexpr int LSP = pk_line_stride(PY);
   const int tid = threadIdx.x;
   const int j = tid % T, ri = tid / T;
   const int unit = blockIdx.x;
   const FilmDev& f = films[find_film(films, lp.nfilms, UK_Y, unit)];
   const int rows = 3 * f.nz * f.Kx;
-  const int row = (unit - f.u0[UK_Y]) * RPB + ri;
-  const bool ok = row < rows;
+  const int row = ((unit - f.u0[UK_Y]) * RPP + ri) * 2;
+  const bool ok0 = row < rows, ok1 = row + 1 < rows;
   const int ny = f.ny;
   extern __shared__ float4 smem4[];
-  float2* line = reinterpret_cast<float2*>(smem4) + ri * LS;
-  float2* S = f.S + (size_t)(ok ? row : 0) * f.srow;
+  float4* sp = smem4 + ri * LSP;
+  GRACE_DSMEM(f, (size_t)RPP * LSP * sizeof(float4));
+  float2* __restrict__ S0 = f.S + (size_t)(ok0 ? row : 0) * f.srow;
+  float2* __restrict__ S1 = f.S + (size_t)(ok1 ? row + 1 : 0) * f.srow;
   pdl_launch_dependents();
   pdl_wait();
-  float2 v[1][8];
+  PC p[8];
+  float2 unused[8];
+  const float2 zero = make_float2(0.f, 0.f);
   if (DIR < 0) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int y = j + r * T;
-      v[0][r] = (ok && y < ny) ? S[y] : make_float2(0.f, 0.f);
-      v[0][r + 4] = make_float2(0.f, 0.f);
+      p[r] = pc_make((ok0 && y < ny) ? S0[y] : zero, (ok1 && y < ny) ? S1[y] : zero);
+      p[r + 4] = pc_zero();
     }
-    fft_reg<PY, -1, true, 1>(v, j, line, LS, lp.twb);
-    if (ok) {
+    fft_pk<PY, -1, true, 0>(p, unused, j, sp, nullptr, lp.twb);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) S[j + r * T] = v[0][r];
+    for (int r = 0; r < 8; ++r) {
+      if (ok0) S0[j + r * T] = pc_a(p[r]);
+      if (ok1) S1[j + r * T] = pc_b(p[r]);
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[0][r] = ok ? S[j + r * T] : make_float2(0.f, 0.f);
-    fft_reg<PY, +1, false, 1>(v, j, line, LS, lp.twb);
-    if (ok) {
+    for (int r = 0; r < 8; ++r) p[r] = pc_make(ok0 ? S0[j + r * T] : zero, ok1 ? S1[j + r * T] : zero);
+    fft_pk<PY, +1, false, 0>(p, unused, j, sp, nullptr, lp.twb);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int y = j + r * T;
-        if (y < ny) S[y] = v[0][r];
+    for (int r = 0; r < 4; ++r) {
+      const int y = j + r * T;
+      if (y < ny) {
+        if (ok0) S0[y] = pc_a(p[r]);
+        if (ok1) S1[y] = pc_b(p[r]);
       }
     }
   }
 }
 
-template <int PZ>
-__global__ void __launch_bounds__(256, 2) kz_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+// z-pass blocks of NT threads (256 or 128; at least one column of Pz/8 threads): 3 or 5
+// resident per SM
+__host__ __device__ constexpr int z_threads(int PZ, int NT) { return NT / (PZ / 8) < 1 ? PZ / 8 : NT; }
+
+template <int PZ, int NT>
+__global__ void __launch_bounds__(z_threads(PZ, NT), NT == 128 ? 5 : 3)
+    kz_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = PZ / 8;
-  constexpr int LS = fast_line_stride(PZ, 1);
-  const int TQ = blockDim.x / T;
+  constexpr int NTB = z_threads(PZ, NT);
+  constexpr int TQ = NTB / T;                    // columns per block
+  constexpr int LSP = pk_line_stride(PZ);
+  constexpr int LSC = fast_line_stride(PZ, 1);
   const int tid = threadIdx.x;
   const int qi = tid % TQ, j = tid / TQ;        // q fastest: coalesced global access
   const int unit = blockIdx.x;
   const FilmDev& f = films[find_film(films, lp.nfilms, UK_Z, unit)];
+  // the descriptor's fields in registers (stores to S cannot make them stale)
+  float2* __restrict__ S = f.S;
+  const float* __restrict__ Tt = f.T;
   const int Py = f.Py, Ky = f.Ky, Kz = f.Kz, nz = f.nz;
+  const int lpy = __ffs(Py) - 1;                 // Py is a power of two
   const int ncol = f.Kx * Py;                    // srow == Py on the split path
-  const int q = (unit - f.u0[UK_Z]) * TQ + qi;
+  const int q0 = (unit - f.u0[UK_Z]) * TQ;
+  const int q = q0 + qi;
   const bool ok = q < ncol;
   extern __shared__ float4 smem4[];
-  float2* lines = reinterpret_cast<float2*>(smem4) + qi * LS;   // component c at + c * TQ * LS
-  const int gs = TQ * LS;
+  float4* sp = smem4 + qi * LSP;                                          // pair (x, y)
+  float2* sc = reinterpret_cast<float2*>(smem4 + TQ * LSP) + qi * LSC;     // line z
+  GRACE_DSMEM(f, (size_t)TQ * (LSP * sizeof(float4) + LSC * sizeof(float2)));
   const size_t zs = (size_t)ncol;                // S[(c * nz + z) * ncol + q]
   pdl_launch_dependents();
   {
-    // the block's tensor slots do not depend on the previous kernel: pull them into L2
-    // now so that the loads after the forward transform hit there
-    const int q0 = (unit - f.u0[UK_Z]) * TQ;
+    // the block's tensor points do not depend on the previous kernel: pull them into L2
+    // now so that the loads after the forward transform hit there.  Blocks of at most Py/2
+    // columns share kx, and their |ky| form one run [lo, hi]; wider blocks take whole kx.
     const int q1 = min(q0 + TQ, ncol) - 1;
-    const int kx0 = q0 / Py, kx1 = q1 / Py;
-    const int nrow = 6 * Kz;                       // (slot, kz') rows of Ky floats per kx
-    for (int idx = tid; idx < (kx1 - kx0 + 1) * nrow; idx += blockDim.x) {
-      const int kx = kx0 + idx / nrow, rr = idx % nrow;
-      const int ka = kx == kx0 ? q0 - kx * Py : 0, kb = kx == kx1 ? q1 - kx * Py : Py - 1;
-      // columns ka..kb read slots kyp in [min, max] of their mirror images
-      const int lo = (ka <= Py / 2 && kb >= Py / 2) ? (ka <= Py - kb ? ka : Py - kb)
-                                                    : (kb <= Py / 2 ? ka : Py - kb);
-      const int hi = (ka <= Py / 2 && kb >= Py / 2) ? Py / 2 : (kb <= Py / 2 ? kb : Py - ka);
-      const float* row = f.T + (size_t)kx * f.nslot * Ky + (size_t)rr * Ky;
-      for (int b = lo & ~31; b <= hi; b += 32) prefetch_l2(row + b);
+    const int kxa = q0 >> lpy, kxb = q1 >> lpy;
+    int lo = 0, hi = Py / 2;
+    if (kxa == kxb) {
+      const int ky0 = q0 - (kxa << lpy), ky1 = q1 - (kxa << lpy);
+      if (ky1 < Py / 2) {
+        lo = ky0;
+        hi = ky1;
+      } else if (ky0 >= Py / 2) {
+        lo = Py - ky1;
+        hi = Py - ky0;
+      }
+    }
+    // whole 128-byte lines of each (kx, kz) row that hold points lo..hi (24 bytes each)
+    const int l0 = lo * 24 / 128, lines = ((hi + 1) * 24 + 127) / 128 - l0;
+    const int per_kx = Kz * lines;
+    for (int idx = tid; idx < (kxb - kxa + 1) * per_kx; idx += NTB) {
+      const int kx = kxa + idx / per_kx, r = idx % per_kx, kz = r / lines, l = r - kz * lines;
+      prefetch_l2(reinterpret_cast<const char*>(Tt + ((size_t)kx * Kz + kz) * Ky * 6) + (l0 + l) * 128);
     }
   }
   pdl_wait();
-  float2 v[3][8];
+  PC p[8];
+  float2 c[8];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int z = j + r * T;
-      v[c][r] = (ok && z < nz) ? f.S[(size_t)(c * nz + z) * zs + q] : make_float2(0.f, 0.f);
-      v[c][r + 4] = make_float2(0.f, 0.f);
+  for (int r = 0; r < 4; ++r) {
+    const int z = j + r * T;
+    float2 a = make_float2(0.f, 0.f), b = a, cz = a;
+    if (ok && z < nz) {
+      a = S[(size_t)(0 * nz + z) * zs + q];
+      b = S[(size_t)(1 * nz + z) * zs + q];
+      cz = S[(size_t)(2 * nz + z) * zs + q];
     }
+    p[r] = pc_make(a, b);
+    c[r] = cz;
+    p[r + 4] = pc_zero();
+    c[r + 4] = make_float2(0.f, 0.f);
   }
-  fft_reg<PZ, -1, true, 3>(v, j, lines, gs, lp.twb);
+  fft_pk<PZ, -1, true>(p, c, j, sp, sc, lp.twb);
   if (ok) {
-    const int kx = q / Py, ky = q - kx * Py;
+    const int kx = q >> lpy, ky = q - (kx << lpy);
     const bool ylo = ky <= Py / 2;
     const int kyp = ylo ? ky : Py - ky;
     const float sy = ylo ? 1.f : -1.f;
-    const float* Tq = f.T + (size_t)kx * f.nslot * Ky + kyp;
+    GRACE_DCHECK(f, kx < f.Kx && kyp < Ky, DBG_T_INDEX);
+    const float* Tq = Tt + ((size_t)kx * Kz * Ky + kyp) * 6;    // T[kx][kz][ky][6]
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int kz = j + r * T;
       const bool zlo = kz <= PZ / 2;
       const int kzp = zlo ? kz : PZ - kz;
       const float sz = zlo ? 1.f : -1.f;
-      const float nxx = __ldg(Tq + (size_t)(0 * Kz + kzp) * Ky);
-      const float nyy = __ldg(Tq + (size_t)(1 * Kz + kzp) * Ky);
-      const float nzz = __ldg(Tq + (size_t)(2 * Kz + kzp) * Ky);
-      const float nxy = sy * __ldg(Tq + (size_t)(3 * Kz + kzp) * Ky);
-      const float nxz = sz * __ldg(Tq + (size_t)(4 * Kz + kzp) * Ky);
-      const float nyz = sy * sz * __ldg(Tq + (size_t)(5 * Kz + kzp) * Ky);
-      const float2 mx = v[0][r], my = v[1][r], mz = v[2][r];
-      v[0][r] = make_float2(nxx * mx.x + nxy * my.x + nxz * mz.x, nxx * mx.y + nxy * my.y + nxz * mz.y);
-      v[1][r] = make_float2(nxy * mx.x + nyy * my.x + nyz * mz.x, nxy * mx.y + nyy * my.y + nyz * mz.y);
-      v[2][r] = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
+      const float2* tp = reinterpret_cast<const float2*>(Tq + (size_t)kzp * Ky * 6);
+      const float2 t0 = __ldg(tp), t1 = __ldg(tp + 1), t2 = __ldg(tp + 2);   // xx yy | zz xy | xz yz
+      const float nxx = t0.x, nyy = t0.y, nzz = t1.x, nxy = sy * t1.y, nxz = sz * t2.x, nyz = sy * sz * t2.y;
+      const float2 mx = pc_a(p[r]), my = pc_b(p[r]), mz = c[r];
+      const float2 hx = make_float2(nxx * mx.x + nxy * my.x + nxz * mz.x, nxx * mx.y + nxy * my.y + nxz * mz.y);
+      const float2 hy = make_float2(nxy * mx.x + nyy * my.x + nyz * mz.x, nxy * mx.y + nyy * my.y + nyz * mz.y);
+      c[r] = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
+      p[r] = pc_make(hx, hy);
     }
   }
-  fft_reg<PZ, +1, false, 3>(v, j, lines, gs, lp.twb);
+  fft_pk<PZ, +1, false>(p, c, j, sp, sc, lp.twb);
   if (ok) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int z = j + r * T;
-        if (z < nz) f.S[(size_t)(c * nz + z) * zs + q] = v[c][r];
+    for (int r = 0; r < 4; ++r) {
+      const int z = j + r * T;
+      if (z < nz) {
+        S[(size_t)(0 * nz + z) * zs + q] = pc_a(p[r]);
+        S[(size_t)(1 * nz + z) * zs + q] = pc_b(p[r]);
+        S[(size_t)(2 * nz + z) * zs + q] = c[r];
       }
+    }
   }
 }
 
@@ -162,10 +206,14 @@ cudaError_t y_disp(int dir, const FilmDev* films, const LaunchP& lp, int nunits,
 template <int PZ>
 cudaError_t z_disp(const FilmDev* films, const LaunchP& lp, int nunits, int threads, size_t smem, cudaStream_t s,
                    bool attr) {
-  if (attr)
-    return cudaFuncSetAttribute((const void*)kz_fast<PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
-  return launch_pdl(kz_fast<PZ>, nunits, threads, smem, s, films, lp);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (attr) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)kz_fast<PZ, 256>, a, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)kz_fast<PZ, 128>, a, (int)smem);
+    return e;
+  }
+  if (threads == z_threads(PZ, 128)) return launch_pdl(kz_fast<PZ, 128>, nunits, threads, smem, s, films, lp);
+  return launch_pdl(kz_fast<PZ, 256>, nunits, threads, smem, s, films, lp);
 }
 
 cudaError_t ydispatch(int Py, int dir, const FilmDev* films, const LaunchP& lp, int nunits, int threads,
@@ -202,27 +250,29 @@ cudaError_t zdispatch(int Pz, const FilmDev* films, const LaunchP& lp, int nunit
 
 bool fast_split_supported(int Py, int Pz) { return Py >= 16 && Py <= 2048 && Pz >= 16 && Pz <= 2048; }
 
-// rows per block (y) and columns per block (z) for 256 threads
-int fast_y_rows(int Py) { return std::max(1, 256 / (Py / 8)); }
-int fast_z_cols(int Pz) { return std::max(1, 256 / (Pz / 8)); }
-size_t fast_y_smem(int Py) { return (size_t)fast_y_rows(Py) * fast_line_stride(Py, Py / 8) * sizeof(float2); }
-size_t fast_z_smem(int Pz) { return (size_t)3 * fast_z_cols(Pz) * fast_line_stride(Pz, 1) * sizeof(float2); }
+// rows per block (y: two per pair) and columns per z block (zt = 256 or 128 threads)
+int fast_y_rows(int Py) { return 2 * y_pairs(Py); }
+int fast_z_cols(int Pz, int zt) { return z_threads(Pz, zt) / (Pz / 8); }
+size_t fast_y_smem(int Py) { return (size_t)y_pairs(Py) * pk_line_stride(Py) * sizeof(float4); }
+size_t fast_z_smem(int Pz, int zt) {
+  return (size_t)fast_z_cols(Pz, zt) * (pk_line_stride(Pz) * sizeof(float4) + fast_line_stride(Pz, 1) * sizeof(float2));
+}
 
 cudaError_t configure_fast_split(int Py, int Pz) {
   LaunchP lp{};
   cudaError_t e = ydispatch(Py, 0, nullptr, lp, 0, 0, std::max<size_t>(fast_y_smem(Py), 1), nullptr, true);
-  if (e == cudaSuccess) e = zdispatch(Pz, nullptr, lp, 0, 0, std::max<size_t>(fast_z_smem(Pz), 1), nullptr, true);
+  if (e == cudaSuccess) e = zdispatch(Pz, nullptr, lp, 0, 0, std::max<size_t>(fast_z_smem(Pz, 256), 1), nullptr, true);
   return e;
 }
 
 cudaError_t launch_fast_y(int Py, int dir, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s) {
   if (nunits <= 0) return cudaSuccess;
-  return ydispatch(Py, dir, films, lp, nunits, fast_y_rows(Py) * (Py / 8), fast_y_smem(Py), s, false);
+  return ydispatch(Py, dir, films, lp, nunits, y_threads(Py), fast_y_smem(Py), s, false);
 }
 
-cudaError_t launch_fast_z(int Pz, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s) {
+cudaError_t launch_fast_z(int Pz, int zt, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s) {
   if (nunits <= 0) return cudaSuccess;
-  return zdispatch(Pz, films, lp, nunits, fast_z_cols(Pz) * (Pz / 8), fast_z_smem(Pz), s, false);
+  return zdispatch(Pz, films, lp, nunits, z_threads(Pz, zt), fast_z_smem(Pz, zt), s, false);
 }
 
 }  // namespace grace

@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "cell.cuh"
+#include "debug.cuh"
 #include "fftreg.cuh"
 #include "internal.cuh"
 
@@ -31,7 +32,7 @@ __host__ __device__ constexpr int x_line_stride(int Q, int TY) {
 }
 
 // Shared memory: 3 TY line buffers (x_line_stride float2 each) for the FFT exchanges and
-// the split.  Over the same bytes, at different times: the staged spectrum st[c][k][t]
+// the split.  Over the same bytes, at different times: the staged spectrum st
 // (read by the merge before the first exchange) and hs[3][TY][Q] floats, holding H_demag
 // per cell and, after the update, Ms m of the new state (the line buffers are idle
 // between the inverse transform and the forward one).
@@ -62,18 +63,19 @@ __host__ __device__ constexpr int x_min_blocks(int Q, int TY, int MODE, bool H) 
   return x_helpers(Q, TY, MODE, H) ? 512 / x_threads(Q, TY, MODE, H) : (TY * Q / 8 == 128 ? 6 : 2);
 }
 
-template <int Q, int TY, int MODE, bool H>
-__global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q, TY, MODE, H) : 256,
-                                  x_min_blocks(Q, TY, MODE, H))
-    kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+// One x-pass tile (work unit `unit`) computed by NTB threads of the block, the first
+// TY Q/8 of them transforming; the rest (whole warps) share the other phases.  The block's
+// other threads, if any, must not touch shared memory meanwhile.  Called by kx_fast (one
+// tile per block) and by the persistent batch kernel (tiles of many films in turn).
+template <int Q, int TY, int MODE, int NTB>
+__device__ __forceinline__ void x_tile_body(const FilmDev* __restrict__ films, const LaunchP& lp, int unit) {
   constexpr int T = Q / 8;
   constexpr int NT = TY * T;                         // transforming threads
-  constexpr int NTB = x_threads(Q, TY, MODE, H);     // all threads of the block
+  static_assert(NTB == NT || (NT % 32 == 0 && NTB % NT == 0), "helpers must be whole warps");
   constexpr int LS = x_line_stride(Q, TY);
   const int tid = threadIdx.x;
   const int j = tid % T, ty = tid / T;
   const bool fft_thread = NTB == NT || tid < NT;  // helpers are whole warps past the first NT
-  const int unit = blockIdx.x;
   const FilmDev& f = films[find_film(films, lp.nfilms, UK_X, unit)];
   const int nx = f.nx, ny = f.ny, nz = f.nz;
   const int nyt = (ny + TY - 1) / TY;
@@ -83,6 +85,7 @@ __global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q,
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
   float2* lines = sm + 3 * ty * LS;                              // this thread's 3 lines
+  GRACE_DSMEM(f, (size_t)3 * TY * LS * sizeof(float2));   // covers hs too (LS > Q / 2)
   float* hs = reinterpret_cast<float*>(sm);                      // [3][TY][Q], over the lines
   const float* __restrict__ m = lp.mk ? lp.mk + 3 * f.cell0 : (lp.parity ? f.m1 : f.m0);
   const size_t srow = f.srow;
@@ -105,13 +108,29 @@ __global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q,
   }
   pdl_wait();
 
+  // staged spectrum layout: element (t, r = c (Q + 1) + k) at t RS + r (t-major, TY >= 4:
+  // the merge reads consecutive k of one row without bank conflicts) or at r TY + t (TY = 2:
+  // rows t, t + 1 side by side, one 16-byte copy for both)
+  constexpr int RS = 3 * (Q + 1);
+  constexpr bool TMAJOR = TY >= 4;
   if (demag) {
     // staging S -> shared as asynchronous copies (every load of the block in flight at
-    // once, none holding a register) into st[c][k][t], over the line buffers: the TY rows
-    // of one (c, k) are adjacent in S, so two rows go in one 16-byte copy where the row
-    // length keeps 16-byte alignment and both rows exist
+    // once, none holding a register), over the line buffers.  The TY rows of one (c, k)
+    // are adjacent in S: threads take t fastest, so they come from one sector.
     float2* st = sm;
-    if constexpr (TY >= 2) {
+    if constexpr (TMAJOR) {
+#pragma unroll 4
+      for (int idx = tid; idx < RS * TY; idx += NTB) {
+        const int t = idx % TY, r = idx / TY;                 // r = c (Q + 1) + k
+        const int k = r % (Q + 1), c = r / (Q + 1);
+        float2* dst = st + t * RS + r;
+        GRACE_DCHECK(f, k <= f.Q && z < nz, DBG_S_INDEX);
+        if (y0 + t < ny) cp_async8(dst, Sz + c * sc + (size_t)k * srow + y0 + t);
+        else dst[0] = make_float2(0.f, 0.f);
+      }
+    } else if constexpr (TY >= 2) {
+      // two rows in one 16-byte copy where the row length keeps 16-byte alignment and both
+      // rows exist
       const bool wide = (srow & 1) == 0;
       constexpr int TP = TY / 2;
 #pragma unroll 4
@@ -148,7 +167,9 @@ __global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q,
         const float2 w = twb_at<+1>(lp.twb, 2 * Q, k);   // W^{-k}, P = 2Q
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float2 xk = st[(c * (Q + 1) + k) * TY + ty], xq = st[(c * (Q + 1) + Q - k) * TY + ty];
+          const int ik = c * (Q + 1) + k, iq = c * (Q + 1) + Q - k;
+          const float2 xk = TMAJOR ? st[ty * RS + ik] : st[ik * TY + ty];
+          const float2 xq = TMAJOR ? st[ty * RS + iq] : st[iq * TY + ty];
           const float2 a = cadd(xk, cconj(xq)), b = csub(xk, cconj(xq));
           const float2 wb = cmul(w, b);
           v[c][r] = make_float2(a.x - wb.y, a.y + wb.x);
@@ -351,6 +372,13 @@ __global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q,
       }
     }
   }
+}
+
+template <int Q, int TY, int MODE, bool H>
+__global__ void __launch_bounds__(x_threads(Q, TY, MODE, H) < 256 ? x_threads(Q, TY, MODE, H) : 256,
+                                  x_min_blocks(Q, TY, MODE, H))
+    kx_fast(const FilmDev* __restrict__ films, LaunchP lp) {
+  x_tile_body<Q, TY, MODE, x_threads(Q, TY, MODE, H)>(films, lp, blockIdx.x);
 }
 
 template <int Q, int TY, int MODE>

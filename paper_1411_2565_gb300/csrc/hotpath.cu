@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "cell.cuh"
+#include "debug.cuh"
 #include "fft.cuh"
 #include "internal.cuh"
 
@@ -26,7 +27,15 @@ constexpr int kThreads = 256;
 constexpr int kMaxT = 4;   // FFT tasks per thread: 8 * kMaxT * kThreads points per block
 
 __device__ __forceinline__ size_t s_index(const FilmDev& f, int c, int z, int k, int y) {
+  GRACE_DCHECK(f, c >= 0 && c < 3 && z >= 0 && z < f.nz && k >= 0 && k < f.Kx && y >= 0 && y < f.srow,
+               DBG_S_INDEX);
   return (((size_t)(c * f.nz + z) * f.Kx + k) * f.srow + y);
+}
+
+// checked builds: a flat index into S
+__device__ __forceinline__ size_t s_flat(const FilmDev& f, size_t i) {
+  GRACE_DCHECK(f, i < (size_t)3 * f.nz * f.Kx * f.srow, DBG_S_INDEX);
+  return i;
 }
 
 // ------------------------------------------------------------------ x pass
@@ -44,6 +53,7 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
   extern __shared__ float4 smem4[];
   float2* cb = reinterpret_cast<float2*>(smem4);
   float* rb = reinterpret_cast<float*>(cb + TY * lsx);     // [3][TY][nx]
+  GRACE_DSMEM(f, (size_t)TY * lsx * sizeof(float2) + (size_t)3 * TY * nx * sizeof(float));
   const int tid = threadIdx.x, NT = blockDim.x;
   const float* __restrict__ m = lp.mk ? lp.mk + 3 * f.cell0 : (lp.parity ? f.m1 : f.m0);
   const int twq = Q > 0 ? GRACE_LMAX / (2 * Q) : 0;      // table step for W^k, P = 2Q
@@ -215,6 +225,7 @@ __device__ void yz_product(const FilmDev& f, int kx, float2* buf, int ls) {
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int z = 0; z < NZ; ++z) M[c][z] = buf[(c * NZ + z) * ls + padi(ky)];
+    GRACE_DCHECK(f, kx < f.Kx && kyp < Ky, DBG_T_INDEX);
     product_direct<NZ>(f.T + (size_t)kx * f.nslot * Ky + kyp, Ky, sy, M, H);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -233,11 +244,12 @@ __global__ void __launch_bounds__(kThreads) k_yz(const FilmDev* __restrict__ fil
   const int nl = 3 * nz;
   extern __shared__ float4 smem4[];
   float2* buf = reinterpret_cast<float2*>(smem4);
+  GRACE_DSMEM(f, (size_t)nl * ls * sizeof(float2));
   const int half = Py > 1 ? Py / 2 : 1;
   for (int t = threadIdx.x; t < nl * half; t += blockDim.x) {
     const int line = t / half, y = t - line * half;
     float2 v = make_float2(0.f, 0.f);
-    if (y < ny) v = f.S[((size_t)line * f.Kx + kx) * f.srow + y];
+    if (y < ny) v = f.S[s_flat(f, ((size_t)line * f.Kx + kx) * f.srow + y)];
     buf[line * ls + padi(y)] = v;
   }
   __syncthreads();
@@ -252,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_yz(const FilmDev* __restrict__ fil
   fft_lines<+1, kMaxT>(buf, Py, nl, ls, lp.tw, false, Py >= 2);
   for (int t = threadIdx.x; t < nl * ny; t += blockDim.x) {
     const int line = t / ny, y = t - line * ny;
-    f.S[((size_t)line * f.Kx + kx) * f.srow + y] = buf[line * ls + padi(y)];
+    f.S[s_flat(f, ((size_t)line * f.Kx + kx) * f.srow + y)] = buf[line * ls + padi(y)];
   }
 }
 
@@ -269,11 +281,12 @@ __global__ void __launch_bounds__(kThreads) k_y(const FilmDev* __restrict__ film
   const int ls = line_stride(Py);
   extern __shared__ float4 smem4[];
   float2* buf = reinterpret_cast<float2*>(smem4);
+  GRACE_DSMEM(f, (size_t)nr * ls * sizeof(float2));
   const int nin = DIR < 0 ? (Py > 1 ? Py / 2 : 1) : Py;
   for (int t = threadIdx.x; t < nr * nin; t += blockDim.x) {
     const int r = t / nin, y = t - r * nin;
     float2 v = make_float2(0.f, 0.f);
-    if (DIR > 0 || y < ny) v = f.S[(size_t)(r0 + r) * f.srow + y];
+    if (DIR > 0 || y < ny) v = f.S[s_flat(f, (size_t)(r0 + r) * f.srow + y)];
     buf[r * ls + padi(y)] = v;
   }
   __syncthreads();
@@ -281,7 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_y(const FilmDev* __restrict__ film
   const int nout = DIR < 0 ? Py : ny;
   for (int t = threadIdx.x; t < nr * nout; t += blockDim.x) {
     const int r = t / nout, y = t - r * nout;
-    f.S[(size_t)(r0 + r) * f.srow + y] = buf[r * ls + padi(y)];
+    f.S[s_flat(f, (size_t)(r0 + r) * f.srow + y)] = buf[r * ls + padi(y)];
   }
 }
 
@@ -303,15 +316,16 @@ __global__ void __launch_bounds__(kThreads) k_z(const FilmDev* __restrict__ film
       const bool lo = ky <= Py / 2;
       const int kyp = lo ? ky : Py - ky;
       const float sy = lo ? 1.f : -1.f;
+      GRACE_DCHECK(f, kx < f.Kx && kyp < Ky, DBG_T_INDEX);
       const float* Tk = f.T + (size_t)kx * f.nslot * Ky + kyp;
 #define GRACE_ZDIRECT(NZ)                                                                 \
   {                                                                                       \
     float2 M[3][NZ], H[3][NZ];                                                            \
     for (int c = 0; c < 3; ++c)                                                           \
-      for (int z = 0; z < NZ; ++z) M[c][z] = f.S[(c * nz + z) * zstride + q];             \
+      for (int z = 0; z < NZ; ++z) M[c][z] = f.S[s_flat(f, (c * nz + z) * zstride + q)];  \
     product_direct<NZ>(Tk, Ky, sy, M, H);                                                 \
     for (int c = 0; c < 3; ++c)                                                           \
-      for (int z = 0; z < NZ; ++z) f.S[(c * nz + z) * zstride + q] = H[c][z];             \
+      for (int z = 0; z < NZ; ++z) f.S[s_flat(f, (c * nz + z) * zstride + q)] = H[c][z];  \
   }
       switch (nz) {
         case 1: GRACE_ZDIRECT(1) break;
@@ -327,12 +341,13 @@ __global__ void __launch_bounds__(kThreads) k_z(const FilmDev* __restrict__ film
   const int ls = line_stride(Pz);
   extern __shared__ float4 smem4[];
   float2* buf = reinterpret_cast<float2*>(smem4);   // line (c, qi) at (c * TQ + qi) * ls
+  GRACE_DSMEM(f, (size_t)3 * TQ * ls * sizeof(float2));
   const int half = Pz / 2;
   for (int t = threadIdx.x; t < 3 * half * TQ; t += blockDim.x) {
     const int qi = t % TQ, r = t / TQ, z = r % half, c = r / half;
     const int q = q0 + qi;
     float2 v = make_float2(0.f, 0.f);
-    if (z < nz && q < ncol) v = f.S[(c * nz + z) * zstride + q];
+    if (z < nz && q < ncol) v = f.S[s_flat(f, (c * nz + z) * zstride + q)];
     buf[(c * TQ + qi) * ls + padi(z)] = v;
   }
   __syncthreads();
@@ -351,13 +366,14 @@ __global__ void __launch_bounds__(kThreads) k_z(const FilmDev* __restrict__ film
     const bool ylo = ky <= Py / 2, zlo = kz <= Pz / 2;
     const int kyp = ylo ? ky : Py - ky, kzp = zlo ? kz : Pz - kz;
     const float sy = ylo ? 1.f : -1.f, sz = zlo ? 1.f : -1.f;
-    const float* Tq = f.T + (size_t)kx * f.nslot * Ky + kyp;
-    const float nxx = __ldg(Tq + (size_t)(0 * Kz + kzp) * Ky);
-    const float nyy = __ldg(Tq + (size_t)(1 * Kz + kzp) * Ky);
-    const float nzz = __ldg(Tq + (size_t)(2 * Kz + kzp) * Ky);
-    const float nxy = sy * __ldg(Tq + (size_t)(3 * Kz + kzp) * Ky);
-    const float nxz = sz * __ldg(Tq + (size_t)(4 * Kz + kzp) * Ky);
-    const float nyz = sy * sz * __ldg(Tq + (size_t)(5 * Kz + kzp) * Ky);
+    GRACE_DCHECK(f, kx < f.Kx && kyp < Ky && kzp < Kz, DBG_T_INDEX);
+    const float* Tq = f.T + (((size_t)kx * Kz + kzp) * Ky + kyp) * 6;   // T[kx][kz][ky][6]
+    const float nxx = __ldg(Tq + 0);
+    const float nyy = __ldg(Tq + 1);
+    const float nzz = __ldg(Tq + 2);
+    const float nxy = sy * __ldg(Tq + 3);
+    const float nxz = sz * __ldg(Tq + 4);
+    const float nyz = sy * sz * __ldg(Tq + 5);
     float2* px = buf + (0 * TQ + qi) * ls + padi(kz);
     float2* py = buf + (1 * TQ + qi) * ls + padi(kz);
     float2* pz = buf + (2 * TQ + qi) * ls + padi(kz);
@@ -375,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) k_z(const FilmDev* __restrict__ film
   for (int t = threadIdx.x; t < 3 * nz * TQ; t += blockDim.x) {
     const int qi = t % TQ, r = t / TQ, z = r % nz, c = r / nz;
     const int q = q0 + qi;
-    if (q < ncol) f.S[(c * nz + z) * zstride + q] = buf[(c * TQ + qi) * ls + padi(z)];
+    if (q < ncol) f.S[s_flat(f, (c * nz + z) * zstride + q)] = buf[(c * TQ + qi) * ls + padi(z)];
   }
 }
 

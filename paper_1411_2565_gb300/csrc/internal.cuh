@@ -5,12 +5,13 @@
 //   S     : x-transformed magnetisation / field spectrum [3][nz][Kx][srow] complex,
 //           y contiguous.  Between steps S holds FFT_x(Ms m_n) for the n_y real rows;
 //           the y (and z) passes work on it in place.
-//   T     : demag tensor spectrum [Kx][nslot][Ky] real, shared by films of one shape,
+//   T     : demag tensor spectrum, real, Kx nslot Ky floats, shared by films of one shape,
 //           pre-multiplied by -1/(Px Py [Pz]) so that H^ = T . M^.
-//     direct-z mode (nz <= 4): slots 4*dz + {xx, yy, zz, xy} for dz = 0..nz-1, then
+//     direct-z mode (nz <= 4): T[kx][slot][ky], slots 4*dz + {xx, yy, zz, xy} for dz = 0..nz-1, then
 //       4*nz + 2*(dz-1) + {xz, yz} for dz = 1..nz-1; the xz / yz entries are the
 //       imaginary parts of the (x,y)-transformed tensor at z offset dz.
-//     FFT-z mode: slot comp*Kz + kz for comp in {xx, yy, zz, xy, xz, yz}, kz = 0..Pz/2.
+//     FFT-z mode: T[kx][kz][ky][6], comp in {xx, yy, zz, xy, xz, yz} adjacent, kz = 0..Pz/2
+//       (nslot = 6 Kz floats per (kx, ky), as before).
 //     Components odd in y (xy, yz) change sign for ky > Py/2, odd in z (xz, yz) for
 //     kz > Pz/2 or dz < 0.
 #pragma once
@@ -52,6 +53,7 @@ struct FilmDev {
   const float* T;
   const float* ms_field;   // per-cell Ms of this film or nullptr
   const float* h_field;    // per-cell H_ext of this film or nullptr
+  unsigned* dbg;           // checked builds: failure bits of the device-side checks (debug.cuh)
 };
 
 // x-pass modes: R2C of Ms m; H_eff output; Euler step; the two halves of the adjoint; the
@@ -168,10 +170,10 @@ cudaError_t launch_fast_yz(int Py, int nz, const FilmDev* films, const LaunchP& 
 cudaError_t configure_kernels(size_t smem_x, size_t smem_yz, size_t smem_y, size_t smem_z);
 bool fast_split_supported(int Py, int Pz);
 int fast_y_rows(int Py);
-int fast_z_cols(int Pz);
+int fast_z_cols(int Pz, int zt);   // zt: z-pass block threads, 256 or 128
 cudaError_t configure_fast_split(int Py, int Pz);
 cudaError_t launch_fast_y(int Py, int dir, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s);
-cudaError_t launch_fast_z(int Pz, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s);
+cudaError_t launch_fast_z(int Pz, int zt, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s);
 
 struct TensorJob {
   int nx, ny, nz, Px, Py, Pz, Kx, Ky, Kz, zfft, nslot;

@@ -143,27 +143,32 @@ __global__ void k_dft_axis(const double* __restrict__ in, double* __restrict__ o
   out[((long long)c * outer + o) * K * inner + (long long)k * inner + i] = acc;
 }
 
-// Pack the transformed tensor into T[kx][slot][ky] (FP32), with the (-i)^{#odd axes}
-// factor, the minus sign of H = -N M and the 1/(Px Py [Pz]) inverse-FFT scale.
+// Pack the transformed tensor (FP32), with the (-i)^{#odd axes} factor, the minus sign of
+// H = -N M and the 1/(Px Py [Pz]) inverse-FFT scale: T[kx][slot][ky] for the direct z sum,
+// T[kx][kz][ky][6] (the six components of a point adjacent) with an FFT along z.
 __global__ void k_tensor_pack(const double* __restrict__ F, float* __restrict__ T, int Kx, int Ky,
                               int Zn, int nz, int zfft, int nslot, double scale) {
   const long long total = (long long)Kx * nslot * Ky;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= total) return;
-  const int ky = (int)(gid % Ky);
-  const int slot = (int)((gid / Ky) % nslot);
-  const int kx = (int)(gid / ((long long)Ky * nslot));
-  int comp, zi;
+  int kx, ky, comp, zi;
   if (zfft) {
-    comp = slot / Zn;
-    zi = slot % Zn;
-  } else if (slot < 4 * nz) {
-    comp = slot & 3;
-    zi = slot >> 2;
+    comp = (int)(gid % 6);
+    ky = (int)((gid / 6) % Ky);
+    zi = (int)((gid / (6LL * Ky)) % Zn);
+    kx = (int)(gid / (6LL * Ky * Zn));
   } else {
-    const int s = slot - 4 * nz;
-    comp = 4 + (s & 1);
-    zi = 1 + (s >> 1);
+    ky = (int)(gid % Ky);
+    const int slot = (int)((gid / Ky) % nslot);
+    kx = (int)(gid / ((long long)Ky * nslot));
+    if (slot < 4 * nz) {
+      comp = slot & 3;
+      zi = slot >> 2;
+    } else {
+      const int s = slot - 4 * nz;
+      comp = 4 + (s & 1);
+      zi = 1 + (s >> 1);
+    }
   }
   // xy: (-i)^2 = -1.  xz, yz: (-i)^2 = -1 with an FFT along z; without it one factor
   // -i remains and the stored value is the imaginary part, -F.

@@ -130,6 +130,11 @@ class _Base:
     def set_option(self, option: int, value: int):
         check(self._L.grace_set_option(self.ctx, option, value), "grace_set_option", self.ctx)
 
+    def sync(self):
+        """Wait for the handle's stream; raises GraceError (GRACE_ETIMEOUT) if a grid barrier of
+        the persistent batch launch timed out since the last report (grace_sync)."""
+        check(self._L.grace_sync(self.ctx), "grace_sync", self.ctx)
+
     # -- compute ------------------------------------------------------------------
     def heff(self, mask: int = TERM_ALL, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         if out is None:
@@ -194,17 +199,39 @@ class _Base:
             pass
 
 
+class _Shape:
+    """A film's grid and cell, as the autotuner keys them."""
+
+    def __init__(self, grid, cell):
+        self.grid = tuple(int(g) for g in grid)
+        self.cell = tuple(float(c) for c in cell)
+
+
+def _tuned(films, device, options, tuned):
+    """options as given; with options None and tuned, the autotuner's schedule for these
+    films (its cache, else the shipped GB300 table, else {}: the library's heuristics)."""
+    if options is not None or not tuned:
+        return dict(options or {})
+    from . import autotune
+    return autotune.best(films, device)
+
+
 class Grace(_Base):
-    """One rectangular film (grid (nx, ny, nz), cell (dx, dy, dz) in metres)."""
+    """One rectangular film (grid (nx, ny, nz), cell (dx, dy, dz) in metres).
+
+    ``options`` (GRACE_OPT_* -> value) are applied before the bind; by default (None) the
+    autotuned schedule for this shape is, unless ``tuned=False``.  ``self.options`` holds
+    what was applied."""
 
     def __init__(self, grid, cell, Ms, A, Ku=0.0, alpha=0.1, gamma0=GAMMA0, device="cuda",
-                 stream: Optional[torch.cuda.Stream] = None, options=None):
+                 stream: Optional[torch.cuda.Stream] = None, options=None, tuned=True):
         L = _lib.load()
         ctx = C.c_void_p()
         check(L.grace_create(C.byref(ctx), ivec(grid), dvec(cell), float(Ms), float(A), float(Ku),
                              float(alpha), float(gamma0)), "grace_create")
         self.grid = tuple(int(g) for g in grid)
-        self._init(ctx, device, stream, options)
+        self.options = _tuned([_Shape(grid, cell)], device, options, tuned)
+        self._init(ctx, device, stream, self.options)
 
     @property
     def shape(self):
@@ -213,9 +240,11 @@ class Grace(_Base):
 
 
 class GraceBatch(_Base):
-    """Independent films stepped together; arrays are the films concatenated in order."""
+    """Independent films stepped together; arrays are the films concatenated in order.
+    ``options`` and ``tuned`` as for ``Grace``."""
 
-    def __init__(self, films, device="cuda", stream: Optional[torch.cuda.Stream] = None, options=None):
+    def __init__(self, films, device="cuda", stream: Optional[torch.cuda.Stream] = None, options=None,
+                 tuned=True):
         L = _lib.load()
         ctx = C.c_void_p()
         n = len(films)
@@ -226,7 +255,8 @@ class GraceBatch(_Base):
                                    dvec([f.Ku for f in films]), dvec([f.alpha for f in films]),
                                    dvec([f.gamma0 for f in films])), "grace_batch_create")
         self.films = list(films)
-        self._init(ctx, device, stream, options)
+        self.options = _tuned(self.films, device, options, tuned)
+        self._init(ctx, device, stream, self.options)
         for i, f in enumerate(films):
             check(L.grace_set_film_hext(ctx, i, dvec(f.hext)), "grace_set_film_hext", ctx)
         self.offsets = np.cumsum([0] + [3 * f.ncells for f in films])

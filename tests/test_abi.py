@@ -159,3 +159,23 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.load(str(tmp_path / "libgrace.so"))
+
+
+def test_batch_path_options_are_validated_on_the_host(lib):
+    """GRACE_OPT_PERSISTENT is a planning option (before grace_bind, 0 or 1); the barrier
+    bound and the failure-detection hook take their documented ranges; grace_sync needs a
+    bound handle."""
+    st, ctx = _create(lib)
+    assert st == 0
+    assert lib.grace_set_option(ctx, _lib.OPT_PERSISTENT, 1) == 0
+    assert lib.grace_set_option(ctx, _lib.OPT_PERSISTENT, 2) == EINVAL
+    assert lib.grace_set_option(ctx, _lib.OPT_PERSISTENT, 0) == 0
+    assert lib.grace_set_option(ctx, _lib.OPT_BARRIER_TIMEOUT_US, 999) == EINVAL
+    assert lib.grace_set_option(ctx, _lib.OPT_BARRIER_TIMEOUT_US, 200000) == 0
+    assert lib.grace_set_option(ctx, _lib.OPT_TEST_SKIP_ARRIVE, -2) == EINVAL
+    assert lib.grace_set_option(ctx, _lib.OPT_TEST_SKIP_ARRIVE, 3) == 0
+    assert lib.grace_set_option(ctx, _lib.OPT_TEST_SKIP_ARRIVE, -1) == 0
+    assert lib.grace_set_option(ctx, _lib.OPT_TILE_Z, 2) == EINVAL
+    assert lib.grace_set_option(ctx, _lib.OPT_SIDE_STREAMS, 0) == 0
+    assert lib.grace_sync(ctx) == ESTATE
+    assert lib.grace_destroy(ctx) == 0

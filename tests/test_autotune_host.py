@@ -45,6 +45,31 @@ def test_local_cache_takes_precedence(gb300):
     mine = {str(_lib.OPT_TILE_X): 0, str(_lib.OPT_TILE_YZ): 1, str(_lib.OPT_GRAPH_STEPS): 8,
             str(_lib.OPT_PDL): 0}
     at._store({key: {"options": mine, "ms_per_step": 1.0, "films": 1, "tried": 1}})
-    assert at.best(films) == {int(k): v for k, v in mine.items()}
+    want = dict(at.DEFAULTS)
+    want.update({int(k): v for k, v in mine.items()})
+    assert at.best(films) == want              # options the entry predates keep their defaults
     with open(at.CACHE) as fh:
         assert json.load(fh)[key]["options"] == mine
+
+
+def test_only_options_that_can_matter_are_searched():
+    film = workloads.film_large().films
+    block = workloads.block().films
+    ens = workloads.ensemble().films
+    assert at.relevant(film)[_lib.OPT_TILE_YZ] and not at.relevant(film)[_lib.OPT_TILE_Z]
+    assert at.relevant(block)[_lib.OPT_TILE_Z] and not at.relevant(block)[_lib.OPT_TILE_YZ]
+    assert at.relevant(ens)[_lib.OPT_SIDE_STREAMS] and not at.relevant(film)[_lib.OPT_SIDE_STREAMS]
+    for k, v in at.DEFAULTS.items():
+        assert v in at.CANDIDATES[k]
+
+
+def test_binding_applies_the_tuned_schedule_unless_told_not_to(gb300, monkeypatch):
+    from paper_1411_2565_gb300 import grace
+    films = workloads.block().films
+    f = films[0]
+    shape = grace._Shape(f.grid, f.cell)
+    assert at._key([shape], torch.device("cuda")) == at._key(films, torch.device("cuda"))
+    assert grace._tuned([shape], "cuda", None, True) == at.best(films)
+    assert grace._tuned([shape], "cuda", None, False) == {}
+    mine = {_lib.OPT_TILE_X: 1}
+    assert grace._tuned([shape], "cuda", mine, True) == mine

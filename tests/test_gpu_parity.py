@@ -261,14 +261,21 @@ def test_ensemble_films_full_trajectory():
             picked.append(k)
     films = [w.films[k] for k in picked]
     m0s = [w.m0[k] for k in picked]
-    gb = GraceBatch(films, device=DEV)
-    gb.set_m(torch.from_numpy(np.concatenate([m.reshape(-1) for m in m0s])).to(DEV))
-    gb.step(w.steps, w.dt)
-    parts = gb.split(gb.get_m())
-    for f, m0, mg in zip(films, m0s, parts):
+    mdev = torch.from_numpy(np.concatenate([m.reshape(-1) for m in m0s])).to(DEV)
+    runs = []
+    for persistent in (0, 1):          # grouped launches, and the one persistent launch
+        gb = GraceBatch(films, device=DEV, options={_lib.OPT_PERSISTENT: persistent})
+        gb.set_m(mdev)
+        gb.step(w.steps, w.dt)
+        gb.sync()
+        runs.append(gb.split(gb.get_m()))
+        gb.close()
+    for k, (f, m0) in enumerate(zip(films, m0s)):
         mo = llg.run(m0, params(f), w.dt, w.steps)
-        d = np.abs(mg.cpu().numpy().reshape(3, -1).mean(1) - mo.reshape(3, -1).mean(1)).max()
-        assert d <= 1e-4, (f.grid, d)
+        for parts in runs:
+            mg = parts[k]
+            d = np.abs(mg.cpu().numpy().reshape(3, -1).mean(1) - mo.reshape(3, -1).mean(1)).max()
+            assert d <= 1e-4, (f.grid, d)
 
 
 def test_adjoint_film_forward_4096_steps():
