@@ -65,15 +65,17 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the block / ensemble / adjoint measurements")
     ap.add_argument("--profile-run", default=None,
-                    choices=["film_large", "block", "film_small", "adjoint_film", "ensemble"],
+                    choices=["film_large", "block", "film_small", "adjoint_film", "ensemble",
+                             "ensemble_persistent"],
                     help="no measurement: take --steps plain-launch steps of this workload (for ncu)")
     return ap.parse_args()
 
 
 def profile_run(name, steps):
     """Plain launches (no graphs) of `steps` steps, so that a profiler sees every kernel.
-    ensemble: the 256-film batch; adjoint_film: `steps` forward steps, then the discrete
-    adjoint of those steps (checkpoints every 16)."""
+    ensemble: the 256-film batch (ensemble_persistent: the same batch in one persistent
+    launch); adjoint_film: `steps` forward steps, then the discrete adjoint of those steps
+    (checkpoints every 16)."""
     import numpy as np
     import torch
     import workloads
@@ -81,9 +83,14 @@ def profile_run(name, steps):
     from paper_1411_2565_gb300.build import build
     from paper_1411_2565_gb300.grace import Grace, GraceBatch
     build()
+    persistent = name == "ensemble_persistent"
+    if persistent:
+        name = "ensemble"
     w = getattr(workloads, name)()
     opts = {_lib.OPT_GRAPH: 0}
     if name == "ensemble":
+        if persistent:
+            opts[_lib.OPT_PERSISTENT] = 1      # one cooperative launch per call
         g = GraceBatch(w.films, device="cuda:0", options=opts)
         g.set_m(torch.from_numpy(np.concatenate([m.reshape(-1) for m in w.m0])).cuda())
         g.step(steps, w.dt)

@@ -6,9 +6,11 @@ one line or the larger compiled tile; kx columns per fused y block; z-pass block
 or 128 threads, i.e. 16 or 8 columns of a 128-point transform), the batch grouping (the
 launch groups of an ensemble stepping side by side on streams of their own, one after
 another, or all in one persistent cooperative launch) and the steps per captured CUDA graph.
-Options that cannot affect the films (a z tile for films without an FFT along z, side
-streams for one film) keep their defaults instead of multiplying the search; programmatic
-dependent launch stays on (captured graphs, which the timings replay, do not use it, and
+A single film is timed the way the benchmark steps it — single steps, L2 flushed before
+each — and a batch by warm replays of captured graphs, the way an ensemble is stepped.
+Options that cannot affect the timing (a z tile for films without an FFT along z, side
+streams and the graph length for one film) keep their defaults instead of multiplying
+the search; programmatic dependent launch stays on (captured graphs do not use it, and
 for single-step calls it measured faster).
 
 Results are cached in a JSON file keyed by the film shapes and the device name.
@@ -55,7 +57,7 @@ def relevant(films) -> Dict[int, bool]:
     batch = len(films) > 1
     return {_lib.OPT_TILE_X: True, _lib.OPT_TILE_YZ: thin, _lib.OPT_TILE_Z: thick,
             _lib.OPT_SIDE_STREAMS: batch, _lib.OPT_PERSISTENT: batch and thin and not thick,
-            _lib.OPT_GRAPH_STEPS: True, _lib.OPT_PDL: False}
+            _lib.OPT_GRAPH_STEPS: batch, _lib.OPT_PDL: False}
 
 
 def _key(films, device) -> str:
@@ -79,7 +81,14 @@ def _store(d: Dict):
     os.replace(tmp, CACHE)
 
 
+L2_FLUSH_BYTES = 256 << 20   # more than the GB300's 129 MB L2
+
+
 def _time(films, m0s, dt, options, device, steps=64, reps=3) -> float:
+    """ms per step of these films under `options`.  One film: single steps with L2 flushed
+    before each (a large film's step in production finds little of its data in L2, and a
+    small film's launch latency shows); a batch: warm replays of captured graphs (how an
+    ensemble is stepped)."""
     from .grace import Grace, GraceBatch
     bind = {k: v for k, v in options.items() if k in BIND_OPTIONS}
     if len(films) == 1:
@@ -93,6 +102,18 @@ def _time(films, m0s, dt, options, device, steps=64, reps=3) -> float:
             g.set_option(k, v)
     g.set_m(torch.from_numpy(np.concatenate([m.reshape(-1) for m in m0s])).to(device))
     g.step(steps, dt)
+    if len(films) == 1:
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            g.step(1, dt)
+            b.record()
+        torch.cuda.synchronize()
+        g.close()
+        return float(np.median([a.elapsed_time(b) for a, b in ev]))
     best = float("inf")
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

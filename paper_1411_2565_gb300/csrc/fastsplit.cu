@@ -22,13 +22,18 @@
 namespace grace {
 namespace {
 
-// y pass: RPP pairs of rows per block (128 threads where the row allows, 6 blocks per SM),
-// Py/8 threads per pair, the two rows of a pair as a packed lane pair (fftpk.cuh)
-__host__ __device__ constexpr int y_pairs(int PY) { return 128 / (PY / 8) < 1 ? 1 : 128 / (PY / 8); }
+// y pass: RPP pairs of rows per block (64 threads where the row allows, 12 blocks per SM;
+// measured on the 512-point rows of the 256x256x64 block: 64-thread blocks 50.3 / 51.6 us
+// forward / inverse, 128-thread blocks at 6 per SM 51.9 / 51.9 us), Py/8 threads per pair,
+// the two rows of a pair as a packed lane pair (fftpk.cuh)
+__host__ __device__ constexpr int y_pairs(int PY) { return 64 / (PY / 8) < 1 ? 1 : 64 / (PY / 8); }
 __host__ __device__ constexpr int y_threads(int PY) { return y_pairs(PY) * (PY / 8); }
+__host__ __device__ constexpr int y_min_blocks(int PY) {
+  return y_threads(PY) <= 64 ? 12 : (y_threads(PY) <= 128 ? 6 : 3);
+}
 
 template <int PY, int DIR>
-__global__ void __launch_bounds__(y_threads(PY), y_threads(PY) <= 128 ? 6 : 3)
+__global__ void __launch_bounds__(y_threads(PY), y_min_blocks(PY))
     ky_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = PY / 8;
   constexpr int RPP = y_pairs(PY);
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(y_threads(PY), y_threads(PY) <= 128 ? 6 : 3)
 __host__ __device__ constexpr int z_threads(int PZ, int NT) { return NT / (PZ / 8) < 1 ? PZ / 8 : NT; }
 
 template <int PZ, int NT>
-__global__ void __launch_bounds__(z_threads(PZ, NT), NT == 128 ? 5 : 3)
+__global__ void __launch_bounds__(z_threads(PZ, NT), z_threads(PZ, NT) <= 128 ? 5 : 3)
     kz_fast(const FilmDev* __restrict__ films, LaunchP lp) {
   constexpr int T = PZ / 8;
   constexpr int NTB = z_threads(PZ, NT);
@@ -95,11 +100,7 @@ __global__ void __launch_bounds__(z_threads(PZ, NT), NT == 128 ? 5 : 3)
   const int qi = tid % TQ, j = tid / TQ;        // q fastest: coalesced global access
   const int unit = blockIdx.x;
   const FilmDev& f = films[find_film(films, lp.nfilms, UK_Z, unit)];
-  // the descriptor's fields in registers (stores to S cannot make them stale)
-  float2* __restrict__ S = f.S;
-  const float* __restrict__ Tt = f.T;
-  const int Py = f.Py, Ky = f.Ky, Kz = f.Kz, nz = f.nz;
-  const int lpy = __ffs(Py) - 1;                 // Py is a power of two
+  const int Kz = f.Kz, Ky = f.Ky, nz = f.nz, Py = f.Py, lpy = __ffs(Py) - 1;   // Py: a power of two
   const int ncol = f.Kx * Py;                    // srow == Py on the split path
   const int q0 = (unit - f.u0[UK_Z]) * TQ;
   const int q = q0 + qi;
@@ -110,29 +111,21 @@ __global__ void __launch_bounds__(z_threads(PZ, NT), NT == 128 ? 5 : 3)
   GRACE_DSMEM(f, (size_t)TQ * (LSP * sizeof(float4) + LSC * sizeof(float2)));
   const size_t zs = (size_t)ncol;                // S[(c * nz + z) * ncol + q]
   pdl_launch_dependents();
-  {
+  if (TQ <= Py / 2) {
     // the block's tensor points do not depend on the previous kernel: pull them into L2
-    // now so that the loads after the forward transform hit there.  Blocks of at most Py/2
-    // columns share kx, and their |ky| form one run [lo, hi]; wider blocks take whole kx.
-    const int q1 = min(q0 + TQ, ncol) - 1;
-    const int kxa = q0 >> lpy, kxb = q1 >> lpy;
-    int lo = 0, hi = Py / 2;
-    if (kxa == kxb) {
-      const int ky0 = q0 - (kxa << lpy), ky1 = q1 - (kxa << lpy);
-      if (ky1 < Py / 2) {
-        lo = ky0;
-        hi = ky1;
-      } else if (ky0 >= Py / 2) {
-        lo = Py - ky1;
-        hi = Py - ky0;
-      }
+    // now so that the loads after the forward transform hit there.  The block's columns
+    // share kx (TQ divides Py/2) and their |ky| form one run [lo, hi]; per (kx, kz) row,
+    // the 128-byte lines that hold points lo..hi (24 bytes each)
+    const int kx = q0 >> lpy, ky0 = q0 - (kx << lpy), ky1 = ky0 + TQ - 1;
+    int lo = ky0, hi = ky1;
+    if (ky0 >= Py / 2) {
+      lo = Py - ky1;
+      hi = Py - ky0;
     }
-    // whole 128-byte lines of each (kx, kz) row that hold points lo..hi (24 bytes each)
     const int l0 = lo * 24 / 128, lines = ((hi + 1) * 24 + 127) / 128 - l0;
-    const int per_kx = Kz * lines;
-    for (int idx = tid; idx < (kxb - kxa + 1) * per_kx; idx += NTB) {
-      const int kx = kxa + idx / per_kx, r = idx % per_kx, kz = r / lines, l = r - kz * lines;
-      prefetch_l2(reinterpret_cast<const char*>(Tt + ((size_t)kx * Kz + kz) * Ky * 6) + (l0 + l) * 128);
+    for (int idx = tid; idx < Kz * lines; idx += NTB) {
+      const int kz = idx / lines, l = idx - kz * lines;
+      prefetch_l2(reinterpret_cast<const char*>(f.T + ((size_t)kx * Kz + kz) * Ky * 6) + (l0 + l) * 128);
     }
   }
   pdl_wait();
@@ -143,9 +136,9 @@ __global__ void __launch_bounds__(z_threads(PZ, NT), NT == 128 ? 5 : 3)
     const int z = j + r * T;
     float2 a = make_float2(0.f, 0.f), b = a, cz = a;
     if (ok && z < nz) {
-      a = S[(size_t)(0 * nz + z) * zs + q];
-      b = S[(size_t)(1 * nz + z) * zs + q];
-      cz = S[(size_t)(2 * nz + z) * zs + q];
+      a = f.S[(size_t)(0 * nz + z) * zs + q];
+      b = f.S[(size_t)(1 * nz + z) * zs + q];
+      cz = f.S[(size_t)(2 * nz + z) * zs + q];
     }
     p[r] = pc_make(a, b);
     c[r] = cz;
@@ -159,7 +152,7 @@ __global__ void __launch_bounds__(z_threads(PZ, NT), NT == 128 ? 5 : 3)
     const int kyp = ylo ? ky : Py - ky;
     const float sy = ylo ? 1.f : -1.f;
     GRACE_DCHECK(f, kx < f.Kx && kyp < Ky, DBG_T_INDEX);
-    const float* Tq = Tt + ((size_t)kx * Kz * Ky + kyp) * 6;    // T[kx][kz][ky][6]
+    const float* Tq = f.T + ((size_t)kx * Kz * Ky + kyp) * 6;    // T[kx][kz][ky][6]
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int kz = j + r * T;
@@ -182,9 +175,9 @@ __global__ void __launch_bounds__(z_threads(PZ, NT), NT == 128 ? 5 : 3)
     for (int r = 0; r < 4; ++r) {
       const int z = j + r * T;
       if (z < nz) {
-        S[(size_t)(0 * nz + z) * zs + q] = pc_a(p[r]);
-        S[(size_t)(1 * nz + z) * zs + q] = pc_b(p[r]);
-        S[(size_t)(2 * nz + z) * zs + q] = c[r];
+        f.S[(size_t)(0 * nz + z) * zs + q] = pc_a(p[r]);
+        f.S[(size_t)(1 * nz + z) * zs + q] = pc_b(p[r]);
+        f.S[(size_t)(2 * nz + z) * zs + q] = c[r];
       }
     }
   }

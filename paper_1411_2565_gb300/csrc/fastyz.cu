@@ -11,7 +11,7 @@ namespace {
 
 template <int PY, int NZ>
 __global__ void __launch_bounds__(256, 3) kyz_fast(const FilmDev* __restrict__ films, LaunchP lp) {
-  yz_tile_body<PY, NZ>(films, lp, blockIdx.x, blockDim.x / (NZ * (PY / 8)), blockDim.x);
+  yz_tile_body<PY, NZ, true>(films, lp, blockIdx.x, blockDim.x / (NZ * (PY / 8)), blockDim.x);
 }
 
 template <int PY, int NZ>

@@ -79,14 +79,17 @@ __device__ __forceinline__ void product_at(float2* base, int LS, const float (&t
 // the row threads, these must be a whole number of warps (no warp may be split between
 // the transform's barriers and the barrier-only path).  Called by kyz_fast (NTH = the
 // tile's threads) and by the persistent batch kernel.
-template <int PY, int NZ>
+// ALL_ROWS: every thread of the block owns a row (NTH = KPB NZ Py/8); the row / barrier-only
+// split then folds away at compile time (a runtime split costs the transforms' registers:
+// measured 96-480 bytes of spills per thread and 27 % on the 1024x256x4 film).
+template <int PY, int NZ, bool ALL_ROWS>
 __device__ __forceinline__ void yz_tile_body(const FilmDev* __restrict__ films, const LaunchP& lp, int unit,
                                              int KPB, int NTH) {
   constexpr int T = PY / 8;
   constexpr int NL = 3 * NZ;
   constexpr int LS = fast_line_stride(PY, T);
   const int tid = threadIdx.x;
-  const bool row_thread = tid < KPB * NZ * T;
+  const bool row_thread = ALL_ROWS || tid < KPB * NZ * T;
   const int j = tid % T;
   const int gi = row_thread ? tid / T : 0;   // kxi * NZ + z
   const int z = gi % NZ;

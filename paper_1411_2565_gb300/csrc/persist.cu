@@ -36,7 +36,7 @@ __device__ __noinline__ void x_unit(const FilmDev* films, const LaunchP& lp, int
 
 template <int PY, int NZ>
 __device__ __noinline__ void yz_unit(const FilmDev* films, const LaunchP& lp, int unit, int kpb) {
-  yz_tile_body<PY, NZ>(films, lp, unit, kpb, kPersistThreads);
+  yz_tile_body<PY, NZ, false>(films, lp, unit, kpb, kPersistThreads);
 }
 
 __device__ void x_dispatch(int kind, const FilmDev* films, const LaunchP& lp, int unit) {
