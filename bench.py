@@ -74,8 +74,8 @@ def parse():
 def profile_run(name, steps):
     """Plain launches (no graphs) of `steps` steps, so that a profiler sees every kernel.
     ensemble: the 256-film batch (ensemble_persistent: the same batch in one persistent
-    launch); adjoint_film: `steps` forward steps, then the discrete adjoint of those steps
-    (checkpoints every 16)."""
+    launch); adjoint_film: `steps` forward steps keeping checkpoints every 16, then the
+    discrete adjoint of those steps from them."""
     import numpy as np
     import torch
     import workloads
@@ -106,13 +106,14 @@ def profile_run(name, steps):
         g.set_hext_field(torch.zeros(3 * f.ncells, device="cuda:0"))
     md = torch.from_numpy(m0.reshape(-1)).cuda()
     g.set_m(md)
-    g.step(steps, w.dt)
     if name == "adjoint_film":
+        tape = g.step_checkpointed(steps, w.dt, 16)
         lam = torch.full((3 * f.ncells,), 1e-6, device="cuda:0")
         gh = torch.zeros(3 * f.ncells, device="cuda:0")
         gm = torch.zeros(f.ncells, device="cuda:0")
-        g.set_m(md)
-        g.backward(lam, steps, w.dt, 16, gh, gm)
+        g.backward(lam, steps, w.dt, 16, gh, gm, tape=tape)
+    else:
+        g.step(steps, w.dt)
     torch.cuda.synchronize()
     print(json.dumps({"profile_run": name, "steps": steps}), flush=True)
 
@@ -576,7 +577,9 @@ def extra_workloads(dev, headline):
                        "method": "2000 steps back to back (graphs of 16 steps); ~300 MB working set"}
     del gb
     # adjoint film at its stated length: 4,096 forward steps, then the backward pass
-    # (checkpoints every 64)
+    # (checkpoints every 64): the forward that keeps its checkpoints and the adjoint from
+    # them (the autograd path), and the self-contained grace_backward, which collects the
+    # checkpoints in a forward pass of its own
     w = workloads.adjoint_film()
     f, m0 = w.films[0], w.m0[0]
     g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=dev)
@@ -587,19 +590,34 @@ def extra_workloads(dev, headline):
     md = torch.from_numpy(m0.reshape(-1)).to(dev)
     n = w.steps
     g.set_m(md)
+    g.step(n, w.dt)                              # warm-up (graph capture)
+    g.set_m(md)
     t_f = time_events(lambda: g.step(n, w.dt), 1)
     lam = torch.full((3 * f.ncells,), 1e-6, device=dev)
     gh = torch.zeros_like(h)
     gm = torch.zeros_like(ms)
     g.set_m(md)
-    g.backward(lam, n, w.dt, 64, gh, gm)        # warm-up (scratch allocation by torch)
+    tape = g.step_checkpointed(n, w.dt, 64)      # warm-up (scratch allocation by torch)
+    g.backward(lam, n, w.dt, 64, gh, gm, tape=tape)
+    del tape                                     # its block returns to torch's cache for the next tape
+    g.set_m(md)
+    tapes = []
+    t_fc = time_events(lambda: tapes.append(g.step_checkpointed(n, w.dt, 64)), 1)
+    t_bc = time_events(lambda: g.backward(lam, n, w.dt, 64, gh, gm, tape=tapes[-1]), 1)
+    g.backward(lam, n, w.dt, 64, gh, gm)         # warm-up
     t_b = time_events(lambda: g.backward(lam, n, w.dt, 64, gh, gm), 1)
     out["adjoint"] = {"workload": w.name, "steps": n, "unit": UNIT,
-                      "forward_value": f.ncells * n / t_f, "backward_value": f.ncells * n / t_b,
-                      "fwd_plus_bwd_ms_per_step": (t_f + t_b) / n * 1e3,
-                      "backward_over_forward": t_b / t_f,
-                      "method": "forward steps, then grace_backward with checkpoints every 64 "
-                                "(re-computes the forward inside)"}
+                      "forward_value": f.ncells * n / t_f,
+                      "forward_checkpointed_value": f.ncells * n / t_fc,
+                      "backward_value": f.ncells * n / t_bc,
+                      "backward_over_forward": t_bc / t_f,
+                      "fwd_plus_bwd_ms_per_step": (t_fc + t_bc) / n * 1e3,
+                      "self_contained_backward_value": f.ncells * n / t_b,
+                      "self_contained_backward_over_forward": t_b / t_f,
+                      "method": "grace_step (forward), grace_step_checkpointed then "
+                                "grace_backward_checkpointed (backward: re-computes each segment "
+                                "from its checkpoint), checkpoints every 64; self-contained: "
+                                "grace_backward with its own checkpointing forward pass"}
     del g
     out["cufft_demag_comparison"] = {name: cufft_demag_comparison(dev, flush, name)
                                      for name in ("block", "film_large")}

@@ -228,7 +228,9 @@ int grace_energy(grace_ctx *ctx, double out[5], double mavg[3]);
  * Accumulates (adds into) dev_dL_dhext (3*N, gradient w.r.t. a per-cell applied field)
  * and dev_dL_dms (N, gradient w.r.t. a per-cell Ms) when non-NULL, and writes dL/dm_0
  * to dev_dL_dm0 when non-NULL.  The state is left at m_0.  Needs
- * grace_backward_workspace_size() bytes in dev_scratch.  Built for the explicit Euler
+ * grace_backward_workspace_size() bytes in dev_scratch: ceil(n / ckpt_every) checkpoint
+ * states, min(ckpt_every, n) recomputed states and as many demag fields, and five more
+ * state-sized buffers (3*N floats each, rounded up to 256 bytes).  Built for the explicit Euler
  * step and a constant applied field: with GRACE_OPT_INTEGRATOR = 1 or a time envelope
  * set it returns GRACE_EUNSUPPORTED.
  */
@@ -236,6 +238,27 @@ int grace_backward_workspace_size(const grace_ctx *ctx, int n, int ckpt_every, s
 int grace_backward(grace_ctx *ctx, const float *dev_dL_dmT, int n, double dt_s, int ckpt_every,
                    void *dev_scratch, size_t scratch_bytes, float *dev_dL_dhext,
                    float *dev_dL_dms, float *dev_dL_dm0);
+
+/*
+ * grace_step_checkpointed - n Euler steps from the current state m_0, as grace_step (the
+ * state ends at m_n, the host time advances by n dt), keeping m_0, m_ckpt, m_2ckpt, ... in
+ * dev_scratch (grace_backward_workspace_size(n, ckpt_every) bytes, 256-byte aligned).
+ * grace_backward_checkpointed then takes the adjoint of those steps without the forward
+ * pass that grace_backward runs first to collect them.  Same restrictions as
+ * grace_backward.
+ *
+ * grace_backward_checkpointed - as grace_backward, from checkpoints that
+ * grace_step_checkpointed wrote into dev_scratch on this handle with the same n, dt_s
+ * and ckpt_every, with the film parameters, fields and options unchanged since (the state
+ * may differ: it is not read).  Overwrites the rest of dev_scratch, keeps the checkpoints
+ * and leaves the state at m_0.  Like grace_backward, no counterpart in the paper, which
+ * steps forward only (Eq. 3).
+ */
+int grace_step_checkpointed(grace_ctx *ctx, int n, double dt_s, int ckpt_every, void *dev_scratch,
+                            size_t scratch_bytes);
+int grace_backward_checkpointed(grace_ctx *ctx, const float *dev_dL_dmT, int n, double dt_s,
+                                int ckpt_every, void *dev_scratch, size_t scratch_bytes,
+                                float *dev_dL_dhext, float *dev_dL_dms, float *dev_dL_dm0);
 
 /*
  * grace_trace - capacity > 0 turns per-kernel timing on: the next `capacity` kernels

@@ -55,6 +55,8 @@ SIGNATURES = {
     "grace_energy": (_I, [_P, _DP, _DP]),
     "grace_backward_workspace_size": (_I, [_P, _I, _I, C.POINTER(_SZ)]),
     "grace_backward": (_I, [_P, _P, _I, _D, _I, _P, _SZ, _P, _P, _P]),
+    "grace_step_checkpointed": (_I, [_P, _I, _D, _I, _P, _SZ]),
+    "grace_backward_checkpointed": (_I, [_P, _P, _I, _D, _I, _P, _SZ, _P, _P, _P]),
     "grace_set_option": (_I, [_P, _I, C.c_longlong]),
     "grace_trace": (_I, [_P, _I]),
     "grace_trace_read": (_I, [_P, _DP, C.POINTER(C.c_longlong)]),

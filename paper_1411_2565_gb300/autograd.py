@@ -2,10 +2,11 @@
 
 ``llg(m0, hext, ms, g, n, dt)`` returns m after ``n`` Euler steps of film ``g``
 (a ``Grace``) from ``m0`` with a per-cell applied field ``hext`` (3N, A/m) and a per-cell
-saturation magnetisation ``ms`` (N, A/m).  Its backward pass calls the hand-written
-discrete adjoint (grace_backward): states are re-computed from checkpoints every
-``ckpt_every`` steps, and the gradients with respect to m0, hext and ms come back from
-the CUDA kernels.  All tensors are flat FP32 on the film's device.
+saturation magnetisation ``ms`` (N, A/m).  The forward pass keeps every
+``ckpt_every``-th state (grace_step_checkpointed); the backward pass calls the
+hand-written discrete adjoint from those checkpoints (grace_backward_checkpointed):
+states are re-computed between checkpoints, and the gradients with respect to m0, hext
+and ms come back from the CUDA kernels.  All tensors are flat FP32 on the film's device.
 """
 from __future__ import annotations
 
@@ -19,10 +20,10 @@ class LLGFunction(torch.autograd.Function):
         g.set_ms_field(ms)
         g.set_hext_field(hext)
         g.set_m(m0)
-        g.step(n, dt)
+        tape = g.step_checkpointed(n, dt, ckpt_every)
         mT = g.get_m()
         ctx.save_for_backward(m0, hext, ms)
-        ctx.g, ctx.n, ctx.dt, ctx.ckpt = g, n, dt, ckpt_every
+        ctx.g, ctx.n, ctx.dt, ctx.ckpt, ctx.tape = g, n, dt, ckpt_every, tape
         return mT
 
     @staticmethod
@@ -31,10 +32,10 @@ class LLGFunction(torch.autograd.Function):
         g = ctx.g
         g.set_ms_field(ms)
         g.set_hext_field(hext)
-        g.set_m(m0)
         g_h = torch.zeros_like(hext)
         g_ms = torch.zeros_like(ms)
-        g_m0 = g.backward(grad_mT.contiguous().float(), ctx.n, ctx.dt, ctx.ckpt, g_h, g_ms, True)
+        g_m0 = g.backward(grad_mT.contiguous().float(), ctx.n, ctx.dt, ctx.ckpt, g_h, g_ms, True, tape=ctx.tape)
+        ctx.tape = None
         return g_m0, g_h, g_ms, None, None, None, None
 
 

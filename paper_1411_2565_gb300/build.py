@@ -21,8 +21,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrace.so")
 LIB_DEBUG = os.path.join(HERE, "libgrace_debug.so")
-SOURCES = ["fastx_q1024.cu", "fastx_q512.cu", "fastx_q128.cu", "fastx_q8.cu", "fastyz.cu", "fastsplit.cu",
-           "api.cu", "hotpath.cu", "tensor.cu", "fastx.cu", "noalloc.cu", "persist.cu"]
+SOURCES = ["fastx_q1024.cu", "fastx_q512.cu", "fastx_q128.cu", "fastx_q8.cu", "fastx_q32.cu", "fastyz.cu",
+           "fastsplit.cu", "api.cu", "hotpath.cu", "tensor.cu", "fastx.cu", "noalloc.cu", "persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

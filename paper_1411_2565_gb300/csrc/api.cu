@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1238,65 +1239,38 @@ int copy_state(grace_ctx* c, float* dst, const float* src) {
 int grace_backward_workspace_size(const grace_ctx* c, int n, int ckpt_every, size_t* bytes) {
   if (!c || !bytes || n < 0 || ckpt_every < 1) return GRACE_EINVAL;
   const size_t seg = (size_t)std::min(ckpt_every, std::max(n, 1));
-  *bytes = (adj_checkpoints(n, ckpt_every) + seg + 4) * adj_state_bytes(c);
+  *bytes = (adj_checkpoints(n, ckpt_every) + 2 * seg + 5) * adj_state_bytes(c);
   return GRACE_OK;
 }
 
-// Discrete adjoint of n Euler steps (see grace.h).  Memory: one state per checkpoint plus
-// one segment of ckpt_every states, recomputed forward from its checkpoint.  Per backward
-// step k: R2C of Ms m_k, y pass, ADJ1 (H_eff(m_k), normalisation and LLG Jacobians,
-// R2C of nu), y pass, ADJ2 (demag of nu, exchange adjoint, lambda_k).
-int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt, void* scratch,
-                   size_t scratch_bytes, float* g_hext, float* g_ms, float* g_m0) {
-  int st = ready(c, true);
-  if (st) return st;
-  if (!dL_dmT) return fail(c, GRACE_EINVAL, "dL/dm_T pointer is NULL");
-  if (c->integrator != 0) return fail(c, GRACE_EUNSUPPORTED, "the adjoint is built for the Euler integrator");
-  if (c->pulse) return fail(c, GRACE_EUNSUPPORTED, "the adjoint takes a constant applied field");
-  if (n < 0 || ckpt < 1) return fail(c, GRACE_EINVAL, "n must be >= 0 and ckpt_every >= 1");
-  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GRACE_EINVAL, "dt must be positive");
-  size_t need = 0;
-  grace_backward_workspace_size(c, n, ckpt, &need);
-  if (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 255u) || scratch_bytes < need)
-    return fail(c, GRACE_EWORKSPACE, "backward scratch missing, misaligned or smaller than "
-                                     "grace_backward_workspace_size");
-  const float fdt = (float)dt;
-  const size_t sb = adj_state_bytes(c);
-  const int nck = adj_checkpoints(n, ckpt);
-  const int segn = std::min(ckpt, std::max(n, 1));
-  char* base = static_cast<char*>(scratch);
-  auto state = [&](int k) { return reinterpret_cast<float*>(base + (size_t)k * sb); };
-  float* ck0 = state(0);
-  float* seg0 = state(nck);
-  float* lamA = state(nck + segn);
-  float* lamB = state(nck + segn + 1);
-  float* lampart = state(nck + segn + 2);
-  float* nu = state(nck + segn + 3);
-  const bool saved_trace = c->trace;
-  c->trace = false;
-  const size_t sf = sb / sizeof(float);
+namespace {
 
-  // Runs of kernels and copies go through CUDA graphs, captured once per distinct run and
-  // replayed (a small film's step is a few microseconds of work per launch): the `ckpt`
-  // forward steps between checkpoints, and per segment the recompute of its states plus
-  // its backward steps.  A run's graph depends only on the m buffer it starts from and on
-  // which of the two lambda buffers holds lambda_{k+1}; everything that differs between
-  // segments (the checkpoint copied in) stays outside it.  Without graphs (GRACE_OPT_GRAPH
-  // = 0) the same runs are launched directly.
+// Runs of kernels and copies of the adjoint and of the checkpointing forward go through
+// CUDA graphs, captured once per distinct run and replayed (a small film's step is a few
+// microseconds of work per launch): the `ckpt` forward steps between checkpoints, and per
+// segment the recompute of its states plus its backward steps.  A run's graph depends
+// only on the m buffer it starts from and on which of the two lambda buffers holds
+// lambda_{k+1}; everything that differs between segments (the checkpoint copied in)
+// stays outside it.  Without graphs (GRACE_OPT_GRAPH = 0) the same runs are launched
+// directly.  Tracing is off meanwhile.
+struct AdjRunner {
   struct Run {
     int kind, len, parity;
     const float* lam;
     cudaGraphExec_t exec;
   };
+  grace_ctx* c;
   std::vector<Run> runs;
-  auto cleanup = [&]() {
+  bool graphs, saved_trace;
+  explicit AdjRunner(grace_ctx* ctx) : c(ctx), graphs(ctx->use_graph && ctx->cap), saved_trace(ctx->trace) {
+    c->trace = false;
+  }
+  ~AdjRunner() {
     for (auto& r : runs)
       if (r.exec) cudaGraphExecDestroy(r.exec);
-    runs.clear();
     c->trace = saved_trace;
-  };
-  const bool graphs = c->use_graph && c->cap;
-  auto run = [&](int kind, int len, const float* lam, auto&& body) -> int {
+  }
+  int run(int kind, int len, const float* lam, const std::function<cudaError_t(cudaStream_t)>& body) {
     if (!graphs) {
       GRACE_CUDA(c, body(c->stream));
       return GRACE_OK;
@@ -1317,41 +1291,99 @@ int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt
       c->pdl = pdl;
       if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
       if (g) cudaGraphDestroy(g);
-      if (e != cudaSuccess) return cuda_fail(c, e, "backward graph capture");
+      if (e != cudaSuccess) return cuda_fail(c, e, "adjoint graph capture");
       runs.push_back({kind, len, c->parity, lam, exec});
     }
     GRACE_CUDA(c, cudaGraphLaunch(exec, c->stream));
     return GRACE_OK;
-  };
-
-  // forward from m_0, keeping the state at every checkpoint
-  if ((st = copy_state(c, ck0, cur_m(c)))) return cleanup(), st;
-  for (int s = 1; s < nck; ++s) {
+  }
+  // `len` Euler steps from the current state (one run)
+  int steps(int len, float fdt, double dt) {
     const int p0 = c->parity;
-    st = run(0, ckpt, nullptr, [&](cudaStream_t sm) {
-      for (int k = 0; k < ckpt; ++k) {
+    const int st = run(0, len, nullptr, [&](cudaStream_t sm) {
+      for (int k = 0; k < len; ++k) {
         const cudaError_t e = enqueue_step(c, (p0 + k) & 1, fdt, dt, sm);
         if (e != cudaSuccess) return e;
       }
       return cudaSuccess;
     });
-    if (st) return cleanup(), st;
-    c->parity = (p0 + ckpt) & 1;
-    if ((st = copy_state(c, state(s), cur_m(c)))) return cleanup(), st;
+    if (st == GRACE_OK) c->parity = (p0 + len) & 1;
+    return st;
   }
-  if ((st = copy_state(c, lamA, dL_dmT))) return cleanup(), st;
+};
+
+// Checks shared by the adjoint entry points and the checkpointing forward.
+int adj_check(grace_ctx* c, int n, double dt, int ckpt, const void* scratch, size_t scratch_bytes) {
+  int st = ready(c, true);
+  if (st) return st;
+  if (c->integrator != 0) return fail(c, GRACE_EUNSUPPORTED, "the adjoint is built for the Euler integrator");
+  if (c->pulse) return fail(c, GRACE_EUNSUPPORTED, "the adjoint takes a constant applied field");
+  if (n < 0 || ckpt < 1) return fail(c, GRACE_EINVAL, "n must be >= 0 and ckpt_every >= 1");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GRACE_EINVAL, "dt must be positive");
+  size_t need = 0;
+  grace_backward_workspace_size(c, n, ckpt, &need);
+  if (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 255u) || scratch_bytes < need)
+    return fail(c, GRACE_EWORKSPACE, "backward scratch missing, misaligned or smaller than "
+                                     "grace_backward_workspace_size");
+  return GRACE_OK;
+}
+
+// Forward from the current state m_0, keeping m_0, m_ckpt, m_2ckpt, ... in the checkpoint
+// slots of the scratch; with `to_end` the remaining steps to m_n follow (the state is
+// then m_n, else m_{(nck-1) ckpt}).
+int adj_forward(grace_ctx* c, AdjRunner& r, int n, double dt, int ckpt, char* base, bool to_end) {
+  const size_t sb = adj_state_bytes(c);
+  const int nck = adj_checkpoints(n, ckpt);
+  const float fdt = (float)dt;
+  int st = copy_state(c, reinterpret_cast<float*>(base), cur_m(c));
+  for (int s = 1; s < nck && st == GRACE_OK; ++s) {
+    st = r.steps(ckpt, fdt, dt);
+    if (st == GRACE_OK) st = copy_state(c, reinterpret_cast<float*>(base + (size_t)s * sb), cur_m(c));
+  }
+  const int rest = n - (nck - 1) * ckpt;
+  if (st == GRACE_OK && to_end && n > 0 && rest > 0) st = r.steps(rest, fdt, dt);
+  return st;
+}
+
+// Discrete adjoint of n Euler steps from the checkpoints in the scratch (see grace.h).
+// Memory: one state per checkpoint plus one segment of ckpt_every states and their
+// H_demag, recomputed forward from its checkpoint (Euler steps that also store
+// H_demag(m_k)).  Backward through a segment k0 .. k0 + len - 1: ADJ1 of its last step
+// (normalisation and LLG Jacobians at m_k with the stored H_demag, R2C of nu_k), then per
+// step a y pass (demag convolution of nu_k) and ADJ21 (demag and exchange adjoint of nu_k
+// giving lambda_k, then ADJ1 of step k - 1), and last a y pass and ADJ2 of step k0
+// (lambda_k0).  The state is left at m_0.
+int adj_backward(grace_ctx* c, AdjRunner& r, const float* dL_dmT, int n, double dt, int ckpt, char* base,
+                 float* g_hext, float* g_ms, float* g_m0) {
+  int st = GRACE_OK;
+  const float fdt = (float)dt;
+  const size_t sb = adj_state_bytes(c);
+  const int nck = adj_checkpoints(n, ckpt);
+  const int segn = std::min(ckpt, std::max(n, 1));
+  auto state = [&](int k) { return reinterpret_cast<float*>(base + (size_t)k * sb); };
+  float* ck0 = state(0);
+  float* seg0 = state(nck);
+  float* hd0 = state(nck + segn);
+  float* lamA = state(nck + 2 * segn);
+  float* lamB = state(nck + 2 * segn + 1);
+  float* lampart = state(nck + 2 * segn + 2);
+  float* nuA = state(nck + 2 * segn + 3);
+  float* nuB = state(nck + 2 * segn + 4);
+  const size_t sf = sb / sizeof(float);
+  if ((st = copy_state(c, lamA, dL_dmT))) return st;
   for (int s = nck - 1; s >= 0 && n > 0; --s) {
     const int k0 = s * ckpt;
     const int len = std::min(ckpt, n - k0);
     // the segment's checkpoint m_{k0} and its spectrum
-    if ((st = copy_state(c, cur_m(c), state(s)))) return cleanup(), st;
+    if ((st = copy_state(c, cur_m(c), state(s)))) return st;
     const cudaError_t er = enqueue_r2c(c);
-    if (er != cudaSuccess) return cleanup(), cuda_fail(c, er, "R2C launch");
+    if (er != cudaSuccess) return cuda_fail(c, er, "R2C launch");
     const int p0 = c->parity;
-    float* la = lamA;
-    float* lb = lamB;
-    st = run(1, len, lamA, [&](cudaStream_t sm) {
-      // recompute m_{k0} .. m_{k0+len-1} into the segment buffer
+    float* li = lamA;     // lambda_{k0+len}
+    float* lo = lamB;     // lambda_k0 at the end (and lambda_k between launches where ADJ21 is two)
+    st = r.run(1, len, lamA, [&](cudaStream_t sm) {
+      // recompute m_{k0} .. m_{k0+len-1} and their H_demag into the segment buffers (the
+      // last step's m_{k0+len} is not kept)
       int p = p0;
       auto mbuf = [&](int par) {
         return reinterpret_cast<float*>(c->ws + c->o_run + (par ? c->o_m1 : c->o_m0));
@@ -1359,48 +1391,102 @@ int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt
       for (int j = 0; j < len; ++j) {
         cudaError_t e = cudaMemcpyAsync(seg0 + (size_t)j * sf, mbuf(p), (size_t)3 * c->ncell * sizeof(float),
                                         cudaMemcpyDeviceToDevice, sm);
-        if (e == cudaSuccess && j + 1 < len) {
-          e = enqueue_step(c, p, fdt, dt, sm);
-          p ^= 1;
+        for (const auto& g : c->groups) {
+          if (e != cudaSuccess) break;
+          LaunchP lp = group_lp(c, g);
+          lp.parity = p;
+          lp.dt = fdt;
+          lp.adj_hd = hd0 + (size_t)j * sf;
+          e = enqueue_conv(c, g, lp, sm);
+          if (e == cudaSuccess) e = enqueue_x(c, g, XM_STEPH, lp, sm);
         }
         if (e != cudaSuccess) return e;
+        p ^= 1;
       }
       // backward through the segment: lambda_{k+1} -> lambda_k
-      float* li = la;
-      float* lo = lb;
+      float* nu_k = nuA;
+      float* nu_o = nuB;
       for (int j = len - 1; j >= 0; --j) {
+        const int mode = j == len - 1 ? XM_ADJ1 : XM_ADJ21;
         for (const auto& g : c->groups) {
           LaunchP lp = group_lp(c, g);
           lp.dt = fdt;
-          lp.mk = seg0 + (size_t)j * sf;
-          lp.adj_lam_in = li;
           lp.adj_lam_part = lampart;
-          lp.adj_nu = nu;
-          lp.adj_lam_out = lo;
           lp.adj_g_hext = g_hext;
           lp.adj_g_ms = g_ms;
-          cudaError_t e = enqueue_x(c, g, XM_R2C, lp, sm);
-          if (e == cudaSuccess) e = enqueue_conv(c, g, lp, sm);
-          if (e == cudaSuccess) e = enqueue_x(c, g, XM_ADJ1, lp, sm);
-          if (e == cudaSuccess) e = enqueue_conv(c, g, lp, sm);
-          if (e == cudaSuccess) e = enqueue_x(c, g, XM_ADJ2, lp, sm);
+          lp.adj_hd = hd0 + (size_t)j * sf;
+          lp.adj_nu_out = nu_o;
+          cudaError_t e = cudaSuccess;
+          if (mode == XM_ADJ1) {
+            lp.mk = seg0 + (size_t)j * sf;
+            lp.adj_lam_in = li;
+          } else {
+            lp.mk = seg0 + (size_t)(j + 1) * sf;
+            lp.adj_mprev = seg0 + (size_t)j * sf;
+            lp.adj_nu = nu_k;
+            lp.adj_lam_out = lo;
+            e = enqueue_conv(c, g, lp, sm);
+          }
+          if (e == cudaSuccess) e = enqueue_x(c, g, mode, lp, sm);
           if (e != cudaSuccess) return e;
         }
-        std::swap(li, lo);
+        std::swap(nu_k, nu_o);
+      }
+      for (const auto& g : c->groups) {
+        LaunchP lp = group_lp(c, g);
+        lp.dt = fdt;
+        lp.mk = seg0;
+        lp.adj_lam_part = lampart;
+        lp.adj_nu = nu_k;
+        lp.adj_lam_out = lo;
+        lp.adj_g_hext = g_hext;
+        lp.adj_g_ms = g_ms;
+        cudaError_t e = enqueue_conv(c, g, lp, sm);
+        if (e == cudaSuccess) e = enqueue_x(c, g, XM_ADJ2, lp, sm);
+        if (e != cudaSuccess) return e;
       }
       return cudaSuccess;
     });
-    if (st) return cleanup(), st;
-    c->parity = (p0 + len - 1) & 1;
-    if (len & 1) std::swap(lamA, lamB);
+    if (st) return st;
+    c->parity = (p0 + len) & 1;
+    std::swap(lamA, lamB);
   }
-  cleanup();
   if (g_m0 && (st = copy_state(c, g_m0, lamA))) return st;
   // leave the state at m_0
   if ((st = copy_state(c, cur_m(c), ck0))) return st;
   GRACE_CUDA(c, enqueue_r2c(c));
-  c->trace = saved_trace;
   return GRACE_OK;
+}
+
+}  // namespace
+
+int grace_backward(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt, void* scratch,
+                   size_t scratch_bytes, float* g_hext, float* g_ms, float* g_m0) {
+  int st = adj_check(c, n, dt, ckpt, scratch, scratch_bytes);
+  if (st) return st;
+  if (!dL_dmT) return fail(c, GRACE_EINVAL, "dL/dm_T pointer is NULL");
+  char* base = static_cast<char*>(scratch);
+  AdjRunner r(c);
+  if ((st = adj_forward(c, r, n, dt, ckpt, base, false))) return st;
+  return adj_backward(c, r, dL_dmT, n, dt, ckpt, base, g_hext, g_ms, g_m0);
+}
+
+int grace_step_checkpointed(grace_ctx* c, int n, double dt, int ckpt, void* scratch, size_t scratch_bytes) {
+  int st = adj_check(c, n, dt, ckpt, scratch, scratch_bytes);
+  if (st) return st;
+  AdjRunner r(c);
+  if ((st = adj_forward(c, r, n, dt, ckpt, static_cast<char*>(scratch), true))) return st;
+  for (int k = 0; k < n; ++k) c->t += dt;   // as grace_step
+  return GRACE_OK;
+}
+
+int grace_backward_checkpointed(grace_ctx* c, const float* dL_dmT, int n, double dt, int ckpt, void* scratch,
+                                size_t scratch_bytes, float* g_hext, float* g_ms, float* g_m0) {
+  int st = adj_check(c, n, dt, ckpt, scratch, scratch_bytes);
+  if (st) return st;
+  if (!dL_dmT) return fail(c, GRACE_EINVAL, "dL/dm_T pointer is NULL");
+  AdjRunner r(c);
+  return adj_backward(c, r, dL_dmT, n, dt, ckpt, static_cast<char*>(scratch), g_hext, g_ms, g_m0);
 }
 
 int grace_set_option(grace_ctx* c, int option, long long value) {

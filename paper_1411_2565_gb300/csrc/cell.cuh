@@ -279,14 +279,18 @@ __device__ __forceinline__ void cell_apply_pair(const FilmDev& f, const LaunchP&
 //                 + (2Ku/(mu0 Ms)) nu_x x                          (f and H_anis terms)
 // Accumulates dL/dH_ext += nu and the local part of dL/dMs, -nu.(H_exch + H_anis)/Ms;
 // stores lambda_part and nu and returns nu (unit weight), the next demag input.
+// H_demag(m) is the one the forward recompute stored (XM_STEPH).
 // Split into the cell's loads (adj1_load) and the rest (adj1_finish) so that callers can
-// put several cells' loads in flight before using any.
+// put several cells' loads in flight before using any; LAM = false leaves lambda_{k+1} to
+// the caller.
 struct Adj1In {
   CellState loc;          // m, Ms and H_exch + H_anis
   float ex, ey, ez;       // H_ext
   float lx, ly, lz;       // lambda_{k+1}
+  float dx, dy, dz;       // H_demag(m)
 };
 
+template <bool LAM>
 __device__ __forceinline__ Adj1In adj1_load(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
                                             int i, int x, int y, int z) {
   const int N = f.ncell;
@@ -301,21 +305,26 @@ __device__ __forceinline__ Adj1In adj1_load(const FilmDev& f, const LaunchP& lp,
     a.ey += f.h_field[N + i];
     a.ez += f.h_field[2 * N + i];
   }
-  const float* li = lp.adj_lam_in + 3 * f.cell0;
-  a.lx = li[i];
-  a.ly = li[N + i];
-  a.lz = li[2 * N + i];
+  const float* hd = lp.adj_hd + 3 * f.cell0;
+  a.dx = hd[i];
+  a.dy = hd[N + i];
+  a.dz = hd[2 * N + i];
+  if (LAM) {
+    const float* li = lp.adj_lam_in + 3 * f.cell0;
+    a.lx = li[i];
+    a.ly = li[N + i];
+    a.lz = li[2 * N + i];
+  }
   return a;
 }
 
-__device__ __forceinline__ float3 adj1_finish(const FilmDev& f, const LaunchP& lp, int i, const Adj1In& in,
-                                              float hdx, float hdy, float hdz) {
+__device__ __forceinline__ float3 adj1_finish(const FilmDev& f, const LaunchP& lp, int i, const Adj1In& in) {
   const int N = f.ncell;
   const long long o = 3 * f.cell0;
   const CellState& loc = in.loc;
   const float mx = loc.mx, my = loc.my, mz = loc.mz;
   const float rms = __frcp_rn(loc.Ms);
-  const float Hx = hdx + loc.hx + in.ex, Hy = hdy + loc.hy + in.ey, Hz = hdz + loc.hz + in.ez;
+  const float Hx = in.dx + loc.hx + in.ex, Hy = in.dy + loc.hy + in.ey, Hz = in.dz + loc.hz + in.ez;
   const float3 p = cross3(mx, my, mz, Hx, Hy, Hz);               // m x H
   const float3 q = cross3(mx, my, mz, p.x, p.y, p.z);            // m x (m x H)
   const float cdt = f.llg_c * lp.dt;                             // -dt c
@@ -343,7 +352,7 @@ __device__ __forceinline__ float3 adj1_finish(const FilmDev& f, const LaunchP& l
   lp_[i] = lpx;
   lp_[N + i] = lpy;
   lp_[2 * N + i] = lpz;
-  float* nu = lp.adj_nu + o;
+  float* nu = lp.adj_nu_out + o;
   nu[i] = nx_;
   nu[N + i] = ny_;
   nu[2 * N + i] = nz_;
@@ -358,14 +367,15 @@ __device__ __forceinline__ float3 adj1_finish(const FilmDev& f, const LaunchP& l
 }
 
 __device__ __forceinline__ float3 adj1_cell(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
-                                            int i, int x, int y, int z, float hdx, float hdy, float hdz) {
-  return adj1_finish(f, lp, i, adj1_load(f, lp, m, i, x, y, z), hdx, hdy, hdz);
+                                            int i, int x, int y, int z) {
+  return adj1_finish(f, lp, i, adj1_load<true>(f, lp, m, i, x, y, z));
 }
 
 // Second pointwise half: with D = -N * nu (the demag convolution of nu, unit weights),
 //   lambda = lambda_part + Ms D + L(C nu),  C = diag(2A/(mu0 Ms_i))   (D and exchange terms)
 //   dL/dMs += m . D
-// Loads (with the exchange term, which is all loads) in adj2_load, stores in adj2_finish.
+// Loads (with the exchange term, which is all loads) in adj2_load; adj2_finish returns
+// lambda and stores it when STORE.
 struct Adj2In {
   float Ms;
   float3 l;                // L(C nu) at the cell
@@ -403,19 +413,25 @@ __device__ __forceinline__ Adj2In adj2_load(const FilmDev& f, const LaunchP& lp,
   return a;
 }
 
-__device__ __forceinline__ void adj2_finish(const FilmDev& f, const LaunchP& lp, int i, const Adj2In& a, float dx,
-                                            float dy, float dz) {
+template <bool STORE>
+__device__ __forceinline__ float3 adj2_finish(const FilmDev& f, const LaunchP& lp, int i, const Adj2In& a,
+                                              float dx, float dy, float dz) {
   const int N = f.ncell;
-  float* lo = lp.adj_lam_out + 3 * f.cell0;
-  lo[i] = a.px + fmaf(a.Ms, dx, a.l.x);
-  lo[N + i] = a.py + fmaf(a.Ms, dy, a.l.y);
-  lo[2 * N + i] = a.pz + fmaf(a.Ms, dz, a.l.z);
+  const float3 l = make_float3(a.px + fmaf(a.Ms, dx, a.l.x), a.py + fmaf(a.Ms, dy, a.l.y),
+                               a.pz + fmaf(a.Ms, dz, a.l.z));
+  if (STORE) {
+    float* lo = lp.adj_lam_out + 3 * f.cell0;
+    lo[i] = l.x;
+    lo[N + i] = l.y;
+    lo[2 * N + i] = l.z;
+  }
   if (lp.adj_g_ms) lp.adj_g_ms[f.cell0 + i] += a.mx * dx + a.my * dy + a.mz * dz;
+  return l;
 }
 
 __device__ __forceinline__ void adj2_cell(const FilmDev& f, const LaunchP& lp, const float* __restrict__ m,
                                           int i, int x, int y, int z, float dx, float dy, float dz) {
-  adj2_finish(f, lp, i, adj2_load(f, lp, m, i, x, y, z), dx, dy, dz);
+  adj2_finish<true>(f, lp, i, adj2_load(f, lp, m, i, x, y, z), dx, dy, dz);
 }
 
 }  // namespace grace

@@ -49,7 +49,9 @@ __host__ __device__ constexpr int x_tile(int Q) {
 __host__ __device__ constexpr bool x_helper_tile(int Q, int TY) {
   return (TY * Q / 8) % 32 == 0 && TY * Q / 8 <= 64;
 }
-__host__ __device__ constexpr bool x_adjoint(int MODE) { return MODE == XM_ADJ1 || MODE == XM_ADJ2; }
+__host__ __device__ constexpr bool x_adjoint(int MODE) {
+  return MODE == XM_ADJ1 || MODE == XM_ADJ2 || MODE == XM_ADJ21;
+}
 __host__ __device__ constexpr bool x_helpers(int Q, int TY, int MODE, bool H) {
   return x_helper_tile(Q, TY) && (H || x_adjoint(MODE));
 }
@@ -91,7 +93,9 @@ __device__ __forceinline__ void x_tile_body(const FilmDev* __restrict__ films, c
   const size_t srow = f.srow;
   const size_t sc = (size_t)nz * f.Kx * srow;                    // component stride of S
   float2* Sz = f.S + (size_t)z * f.Kx * srow;                    // S[c=0][z][.][.]
-  const bool demag = (MODE == XM_STEP) || (MODE == XM_ADJ1) || (MODE == XM_ADJ2) ||
+  // the cell update of XM_STEPH is XM_STEP's; XM_ADJ1 takes H_demag(m_k) from the store
+  constexpr int CM = MODE == XM_STEPH ? XM_STEP : MODE;
+  const bool demag = (CM == XM_STEP) || (MODE == XM_ADJ2) || (MODE == XM_ADJ21) ||
                      (MODE == XM_HEUN1) || (MODE == XM_HEUN2) ||
                      (MODE == XM_HEFF && (lp.mask & 1u));
 
@@ -190,32 +194,34 @@ __device__ __forceinline__ void x_tile_body(const FilmDev* __restrict__ films, c
     } else {
       fft_reg_barriers<Q>();
     }
-  } else {
+  } else if constexpr (MODE != XM_ADJ1) {
     for (int idx = tid; idx < 3 * TY * Q; idx += NTB) hs[idx] = 0.f;
   }
   __syncthreads();
 
-  if constexpr (MODE == XM_ADJ1 || MODE == XM_ADJ2) {
-    // adjoint halves: H_demag(m_k) -> lambda_part, nu (R2C of nu follows), or D(nu) -> lambda_k;
-    // the loads of UA cells are issued before any of them is finished
-    using AdjIn = std::conditional_t<MODE == XM_ADJ1, Adj1In, Adj2In>;
-    constexpr int UA = 4;
-    for (int base = 0; base < TY * Q; base += UA * NTB) {
-      AdjIn in[UA];
-      bool ok[UA];
+  if constexpr (MODE == XM_ADJ21) {
+    // second half of step k (D(nu_k) -> lambda_k), then the first half of step k - 1 at
+    // m_{k-1} with that lambda_k (-> lambda_part, nu_{k-1}; nu to hs for the R2C): both
+    // halves' loads of UB cells are issued before any cell is finished
+    constexpr int UB = 2;
+    const float* __restrict__ m1 = lp.adj_mprev + 3 * f.cell0;
+    for (int base = 0; base < TY * Q; base += UB * NTB) {
+      Adj2In a2[UB];
+      Adj1In a1[UB];
+      bool ok[UB];
 #pragma unroll
-      for (int u = 0; u < UA; ++u) {
+      for (int u = 0; u < UB; ++u) {
         const int idx = base + u * NTB + tid;
         const int t = idx / Q, x = idx - t * Q, y = y0 + t;
         ok[u] = idx < TY * Q && x < nx && y < ny;
         if (ok[u]) {
           const int i = (z * ny + y) * nx + x;
-          if constexpr (MODE == XM_ADJ1) in[u] = adj1_load(f, lp, m, i, x, y, z);
-          else in[u] = adj2_load(f, lp, m, i, x, y, z);
+          a2[u] = adj2_load(f, lp, m, i, x, y, z);
+          a1[u] = adj1_load<false>(f, lp, m1, i, x, y, z);
         }
       }
 #pragma unroll
-      for (int u = 0; u < UA; ++u) {
+      for (int u = 0; u < UB; ++u) {
         const int idx = base + u * NTB + tid;
         if (idx >= TY * Q) continue;
         const int t = idx / Q, x = idx - t * Q, y = y0 + t;
@@ -223,25 +229,80 @@ __device__ __forceinline__ void x_tile_body(const FilmDev* __restrict__ films, c
         float3 r = make_float3(0.f, 0.f, 0.f);
         if (ok[u]) {
           const int i = (z * ny + y) * nx + x;
-          if constexpr (MODE == XM_ADJ1) r = adj1_finish(f, lp, i, in[u], hp[0], hp[TY * Q], hp[2 * TY * Q]);
-          else adj2_finish(f, lp, i, in[u], hp[0], hp[TY * Q], hp[2 * TY * Q]);
+          const float3 l = adj2_finish<false>(f, lp, i, a2[u], hp[0], hp[TY * Q], hp[2 * TY * Q]);
+          a1[u].lx = l.x;
+          a1[u].ly = l.y;
+          a1[u].lz = l.z;
+          r = adj1_finish(f, lp, i, a1[u]);
         }
         hp[0] = r.x;
         hp[TY * Q] = r.y;
         hp[2 * TY * Q] = r.z;
       }
     }
+  } else if constexpr (x_adjoint(MODE)) {
+    // one adjoint half, the loads of UA cells issued before any of them is finished
+    constexpr int UA = 4;
+    if constexpr (MODE == XM_ADJ2) {
+      // second half of step k: D(nu_k) -> lambda_k
+      for (int base = 0; base < TY * Q; base += UA * NTB) {
+        Adj2In in[UA];
+        bool ok[UA];
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+          const int idx = base + u * NTB + tid;
+          const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+          ok[u] = idx < TY * Q && x < nx && y < ny;
+          if (ok[u]) in[u] = adj2_load(f, lp, m, (z * ny + y) * nx + x, x, y, z);
+        }
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+          const int idx = base + u * NTB + tid;
+          if (!ok[u]) continue;
+          const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+          float* hp = hs + t * Q + x;
+          adj2_finish<true>(f, lp, (z * ny + y) * nx + x, in[u], hp[0], hp[TY * Q], hp[2 * TY * Q]);
+        }
+      }
+    } else {
+      // first half of step k: lambda_{k+1}, m_k and the stored H_demag(m_k) -> lambda_part,
+      // nu_k; nu goes to hs for the R2C
+      for (int base = 0; base < TY * Q; base += UA * NTB) {
+        Adj1In in[UA];
+        bool ok[UA];
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+          const int idx = base + u * NTB + tid;
+          const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+          ok[u] = idx < TY * Q && x < nx && y < ny;
+          if (ok[u]) in[u] = adj1_load<true>(f, lp, m, (z * ny + y) * nx + x, x, y, z);
+        }
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+          const int idx = base + u * NTB + tid;
+          if (idx >= TY * Q) continue;
+          const int t = idx / Q, x = idx - t * Q, y = y0 + t;
+          float* hp = hs + t * Q + x;
+          float3 r = make_float3(0.f, 0.f, 0.f);
+          if (ok[u]) r = adj1_finish(f, lp, (z * ny + y) * nx + x, in[u]);
+          hp[0] = r.x;
+          hp[TY * Q] = r.y;
+          hp[2 * TY * Q] = r.z;
+        }
+      }
+    }
   } else {
   // cell update, one thread per cell of the TY x Q tile (x >= nx, y >= ny give zeros);
   // each thread owns 8 cells and issues the loads of 4 of them before using any
     const unsigned mask =
-        (MODE == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
+        (CM == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
     const float hsc = lp.hscale ? lp.hscale[MODE == XM_HEUN2 ? 1 : 0] : 1.f;
-    // even rows with 8-byte aligned arrays (the caller's H output included): cells in
-    // pairs (x, x + 1), 8-byte loads and stores
+    // even rows with 8-byte aligned arrays (the caller's H output and the H_demag store
+    // included): cells in pairs (x, x + 1), 8-byte loads and stores
     const bool pairs = ((nx | f.cell0) & 1) == 0 &&
                        ((reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(f.ms_field) |
-                         reinterpret_cast<uintptr_t>(f.h_field) | reinterpret_cast<uintptr_t>(lp.out)) & 7) == 0;
+                         reinterpret_cast<uintptr_t>(f.h_field) | reinterpret_cast<uintptr_t>(lp.out) |
+                         reinterpret_cast<uintptr_t>(lp.adj_hd)) & 7) == 0;
     if (pairs) {
       constexpr int QP = Q / 2;
       constexpr int U2 = 2;
@@ -255,8 +316,14 @@ __device__ __forceinline__ void x_tile_body(const FilmDev* __restrict__ films, c
           ok[u] = idx < TY * QP && x < nx && y < ny;
           if (ok[u]) {
             const float2* hp = reinterpret_cast<const float2*>(hs + t * Q + x);
-            cell_field_pair(f, mask, m, (z * ny + y) * nx + x, x, y, z, hp[0], hp[TY * Q / 2], hp[TY * Q], hsc,
-                            ca[u], cb[u]);
+            const int i = (z * ny + y) * nx + x;
+            cell_field_pair(f, mask, m, i, x, y, z, hp[0], hp[TY * Q / 2], hp[TY * Q], hsc, ca[u], cb[u]);
+            if constexpr (MODE == XM_STEPH) {
+              float2* hd = reinterpret_cast<float2*>(lp.adj_hd + 3 * f.cell0 + i);
+              hd[0] = hp[0];
+              hd[f.ncell / 2] = hp[TY * Q / 2];
+              hd[f.ncell] = hp[TY * Q];
+            }
           }
         }
 #pragma unroll
@@ -267,7 +334,7 @@ __device__ __forceinline__ void x_tile_body(const FilmDev* __restrict__ films, c
           float3 ra = make_float3(0.f, 0.f, 0.f), rb = ra;
           if (ok[u]) {
             const int i = (z * ny + y) * nx + x;
-            cell_apply_pair<MODE>(f, lp, i, ca[u], cb[u], ra, rb);
+            cell_apply_pair<CM>(f, lp, i, ca[u], cb[u], ra, rb);
           }
           float2* hp = reinterpret_cast<float2*>(hs + t * Q + x);
           hp[0] = make_float2(ra.x, rb.x);
@@ -287,7 +354,14 @@ __device__ __forceinline__ void x_tile_body(const FilmDev* __restrict__ films, c
         ok[u] = idx < TY * Q && x < nx && y < ny;
         if (ok[u]) {
           const float* hp = hs + t * Q + x;
-          cs[u] = cell_field(f, mask, m, (z * ny + y) * nx + x, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q], hsc);
+          const int i = (z * ny + y) * nx + x;
+          cs[u] = cell_field(f, mask, m, i, x, y, z, hp[0], hp[TY * Q], hp[2 * TY * Q], hsc);
+          if constexpr (MODE == XM_STEPH) {
+            float* hd = lp.adj_hd + 3 * f.cell0;
+            hd[i] = hp[0];
+            hd[f.ncell + i] = hp[TY * Q];
+            hd[2 * f.ncell + i] = hp[2 * TY * Q];
+          }
         }
       }
 #pragma unroll
@@ -296,7 +370,7 @@ __device__ __forceinline__ void x_tile_body(const FilmDev* __restrict__ films, c
         if (idx >= TY * Q) continue;
         const int t = idx / Q, x = idx - t * Q, y = y0 + t;
         float3 r = make_float3(0.f, 0.f, 0.f);
-        if (ok[u]) r = cell_apply<MODE>(f, lp, (z * ny + y) * nx + x, cs[u]);
+        if (ok[u]) r = cell_apply<CM>(f, lp, (z * ny + y) * nx + x, cs[u]);
         float* hp = hs + t * Q + x;
         hp[0] = r.x;
         hp[TY * Q] = r.y;
@@ -409,6 +483,8 @@ cudaError_t launch_qt(int mode, const FilmDev* films, const LaunchP& lp, int nun
     case XM_ADJ2: return launch_qtm<Q, TY, XM_ADJ2>(films, lp, nunits, smem, s);
     case XM_HEUN1: return launch_qtm<Q, TY, XM_HEUN1>(films, lp, nunits, smem, s);
     case XM_HEUN2: return launch_qtm<Q, TY, XM_HEUN2>(films, lp, nunits, smem, s);
+    case XM_STEPH: return launch_qtm<Q, TY, XM_STEPH>(films, lp, nunits, smem, s);
+    case XM_ADJ21: return launch_qtm<Q, TY, XM_ADJ21>(films, lp, nunits, smem, s);
     default: return launch_qtm<Q, TY, XM_STEP>(films, lp, nunits, smem, s);
   }
 }
@@ -422,6 +498,8 @@ cudaError_t attr_qt(size_t smem) {
   if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_ADJ2>(smem);
   if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_HEUN1>(smem);
   if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_HEUN2>(smem);
+  if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_STEPH>(smem);
+  if (e == cudaSuccess) e = attr_qtm<Q, TY, XM_ADJ21>(smem);
   return e;
 }
 

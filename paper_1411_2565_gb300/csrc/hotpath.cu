@@ -58,8 +58,9 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
   const float* __restrict__ m = lp.mk ? lp.mk + 3 * f.cell0 : (lp.parity ? f.m1 : f.m0);
   const int twq = Q > 0 ? GRACE_LMAX / (2 * Q) : 0;      // table step for W^k, P = 2Q
 
-  const bool demag = (MODE == XM_STEP) || (MODE == XM_ADJ1) || (MODE == XM_ADJ2) ||
-                     (MODE == XM_HEUN1) || (MODE == XM_HEUN2) ||
+  // the cell update of XM_STEPH is XM_STEP's; XM_ADJ1 takes H_demag(m_k) from the store
+  constexpr int CM = MODE == XM_STEPH ? XM_STEP : MODE;
+  const bool demag = (CM == XM_STEP) || (MODE == XM_ADJ2) || (MODE == XM_HEUN1) || (MODE == XM_HEUN2) ||
                      (MODE == XM_HEFF && (lp.mask & 1u));
   if (demag) {
     for (int c = 0; c < 3; ++c) {
@@ -116,15 +117,21 @@ __global__ void __launch_bounds__(kThreads) k_xpass(const FilmDev* __restrict__ 
       const int i = (z * ny + y) * nx + x;
       const float hdx = demag ? *r0 : 0.f, hdy = demag ? *r1 : 0.f, hdz = demag ? *r2 : 0.f;
       if constexpr (MODE == XM_ADJ1) {
-        r = adj1_cell(f, lp, m, i, x, y, z, hdx, hdy, hdz);
+        r = adj1_cell(f, lp, m, i, x, y, z);
       } else if constexpr (MODE == XM_ADJ2) {
         adj2_cell(f, lp, m, i, x, y, z, hdx, hdy, hdz);
       } else {
         const unsigned mask =
-        (MODE == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
+        (CM == XM_STEP || MODE == XM_HEUN1 || MODE == XM_HEUN2) ? 15u : (MODE == XM_HEFF ? lp.mask : 0u);
         const float hsc = lp.hscale ? lp.hscale[MODE == XM_HEUN2 ? 1 : 0] : 1.f;
         const CellState cs = cell_field(f, mask, m, i, x, y, z, hdx, hdy, hdz, hsc);
-        r = cell_apply<MODE>(f, lp, i, cs);
+        if constexpr (MODE == XM_STEPH) {
+          float* hd = lp.adj_hd + 3 * f.cell0;
+          hd[i] = hdx;
+          hd[f.ncell + i] = hdy;
+          hd[2 * f.ncell + i] = hdz;
+        }
+        r = cell_apply<CM>(f, lp, i, cs);
       }
     }
     *r0 = r.x;
@@ -509,6 +516,7 @@ cudaError_t configure_kernels(size_t smem_x, size_t smem_yz, size_t smem_y, size
   set((const void*)k_xpass<XM_ADJ2>, smem_x);
   set((const void*)k_xpass<XM_HEUN1>, smem_x);
   set((const void*)k_xpass<XM_HEUN2>, smem_x);
+  set((const void*)k_xpass<XM_STEPH>, smem_x);
   set((const void*)k_yz, smem_yz);
   set((const void*)k_y<-1>, smem_y);
   set((const void*)k_y<+1>, smem_y);
@@ -526,6 +534,16 @@ cudaError_t launch_xpass(int mode, const FilmDev* films, const LaunchP& lp, int 
     case XM_ADJ2: k_xpass<XM_ADJ2><<<nunits, kThreads, smem, s>>>(films, lp); break;
     case XM_HEUN1: k_xpass<XM_HEUN1><<<nunits, kThreads, smem, s>>>(films, lp); break;
     case XM_HEUN2: k_xpass<XM_HEUN2><<<nunits, kThreads, smem, s>>>(films, lp); break;
+    case XM_STEPH: k_xpass<XM_STEPH><<<nunits, kThreads, smem, s>>>(films, lp); break;
+    case XM_ADJ21: {
+      // the second half of step k, then the first of step k - 1 from m_{k-1} and lambda_k
+      k_xpass<XM_ADJ2><<<nunits, kThreads, smem, s>>>(films, lp);
+      LaunchP lp1 = lp;
+      lp1.mk = lp.adj_mprev;
+      lp1.adj_lam_in = lp.adj_lam_out;
+      k_xpass<XM_ADJ1><<<nunits, kThreads, smem, s>>>(films, lp1);
+      break;
+    }
     default: k_xpass<XM_STEP><<<nunits, kThreads, smem, s>>>(films, lp); break;
   }
   return cudaGetLastError();

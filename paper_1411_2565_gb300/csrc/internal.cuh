@@ -57,8 +57,14 @@ struct FilmDev {
 };
 
 // x-pass modes: R2C of Ms m; H_eff output; Euler step; the two halves of the adjoint; the
-// two stages of a Heun step (stage 1 = the Euler predictor that also keeps k1 = f(m_n)).
-enum XMode { XM_R2C = 0, XM_HEFF = 1, XM_STEP = 2, XM_ADJ1 = 3, XM_ADJ2 = 4, XM_HEUN1 = 5, XM_HEUN2 = 6 };
+// two stages of a Heun step (stage 1 = the Euler predictor that also keeps k1 = f(m_n));
+// the Euler step that also stores H_demag(m_n) (the adjoint's recompute); the second
+// adjoint half of step k followed by the first of step k - 1 (one launch where the x pass
+// is fused, two otherwise).
+enum XMode {
+  XM_R2C = 0, XM_HEFF = 1, XM_STEP = 2, XM_ADJ1 = 3, XM_ADJ2 = 4, XM_HEUN1 = 5, XM_HEUN2 = 6,
+  XM_STEPH = 7, XM_ADJ21 = 8
+};
 
 struct LaunchP {
   int nfilms;
@@ -76,11 +82,14 @@ struct LaunchP {
   float* k1;        // Heun: f(m_n), concatenated films (3 N)
   const float* hscale;  // applied-field envelope {s(t_n), s(t_n + dt)}, nullptr: constant field
   // adjoint (concatenated films; nullptr when unused)
-  const float* mk;          // state to read instead of m[parity] (R2C, ADJ1, ADJ2)
-  const float* adj_lam_in;  // lambda_{k+1}
-  float* adj_lam_part;      // ADJ1 -> ADJ2
-  float* adj_nu;            // ADJ1 -> ADJ2
-  float* adj_lam_out;       // lambda_k
+  const float* mk;          // state to read instead of m[parity] (R2C, ADJ1: m_k; ADJ2, ADJ21: m_k)
+  const float* adj_mprev;   // m_{k-1}, the state of ADJ21's first half
+  float* adj_hd;            // H_demag of the first half's state (written by STEPH, read by ADJ1, ADJ21)
+  const float* adj_lam_in;  // lambda_{k+1} (ADJ1)
+  float* adj_lam_part;      // first half -> second half
+  const float* adj_nu;      // nu of the second half's step (ADJ2, ADJ21)
+  float* adj_nu_out;        // nu written by the first half (ADJ1, ADJ21)
+  float* adj_lam_out;       // lambda_k (ADJ2; ADJ21 where it runs as two launches)
   float* adj_g_hext;        // += dL/dH_ext (3 N) or nullptr
   float* adj_g_ms;          // += dL/dMs (N) or nullptr
 };

@@ -148,28 +148,48 @@ class _Base:
     def step(self, n: int, dt: float):
         check(self._L.grace_step(self.ctx, int(n), float(dt)), "grace_step", self.ctx)
 
-    def backward(self, dL_dmT: torch.Tensor, n: int, dt: float, ckpt_every: int = 64,
-                 g_hext: Optional[torch.Tensor] = None, g_ms: Optional[torch.Tensor] = None,
-                 want_m0: bool = True) -> Optional[torch.Tensor]:
-        """Discrete adjoint of ``n`` Euler steps from the current state (grace_backward).
-
-        Adds dL/dH_ext into ``g_hext`` (3N) and dL/dMs into ``g_ms`` (N) when given and
-        returns dL/dm_0; the state is left at m_0."""
+    def _scratch(self, n: int, ckpt_every: int):
         sz = C.c_size_t()
         check(self._L.grace_backward_workspace_size(self.ctx, int(n), int(ckpt_every), C.byref(sz)),
               "grace_backward_workspace_size", self.ctx)
         scratch = torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=self.device)
-        gm0 = torch.empty(3 * self.ncell, dtype=torch.float32, device=self.device) if want_m0 else None
         if self.stream is not None:
-            for t in (scratch, gm0):
-                if t is not None:
-                    t.record_stream(self.stream)
-        check(self._L.grace_backward(
-            self.ctx, _dev_ptr(dL_dmT, 3 * self.ncell, "dL/dm_T"), int(n), float(dt), int(ckpt_every),
-            scratch.data_ptr(), int(sz.value),
-            None if g_hext is None else _dev_ptr(g_hext, 3 * self.ncell, "g_hext"),
-            None if g_ms is None else _dev_ptr(g_ms, self.ncell, "g_ms"),
-            None if gm0 is None else gm0.data_ptr()), "grace_backward", self.ctx)
+            scratch.record_stream(self.stream)
+        return scratch, int(sz.value)
+
+    def step_checkpointed(self, n: int, dt: float, ckpt_every: int = 64) -> "Tape":
+        """``n`` Euler steps as ``step`` that also keep every ``ckpt_every``-th state
+        (grace_step_checkpointed); ``backward(..., tape=)`` then skips its own forward pass."""
+        scratch, nbytes = self._scratch(n, ckpt_every)
+        check(self._L.grace_step_checkpointed(self.ctx, int(n), float(dt), int(ckpt_every),
+                                              scratch.data_ptr(), nbytes), "grace_step_checkpointed", self.ctx)
+        return Tape(scratch, nbytes, int(n), float(dt), int(ckpt_every))
+
+    def backward(self, dL_dmT: torch.Tensor, n: int, dt: float, ckpt_every: int = 64,
+                 g_hext: Optional[torch.Tensor] = None, g_ms: Optional[torch.Tensor] = None,
+                 want_m0: bool = True, tape: Optional["Tape"] = None) -> Optional[torch.Tensor]:
+        """Discrete adjoint of ``n`` Euler steps (grace_backward): from the current state, or
+        with ``tape`` from the checkpoints of ``step_checkpointed`` (same n, dt, ckpt_every;
+        grace_backward_checkpointed).
+
+        Adds dL/dH_ext into ``g_hext`` (3N) and dL/dMs into ``g_ms`` (N) when given and
+        returns dL/dm_0; the state is left at m_0."""
+        if tape is not None:
+            if (tape.n, tape.dt, tape.ckpt_every) != (int(n), float(dt), int(ckpt_every)):
+                raise ValueError("the tape was recorded with another n, dt or ckpt_every")
+            scratch, nbytes = tape.scratch, tape.nbytes
+            fn, name = self._L.grace_backward_checkpointed, "grace_backward_checkpointed"
+        else:
+            scratch, nbytes = self._scratch(n, ckpt_every)
+            fn, name = self._L.grace_backward, "grace_backward"
+        gm0 = torch.empty(3 * self.ncell, dtype=torch.float32, device=self.device) if want_m0 else None
+        if self.stream is not None and gm0 is not None:
+            gm0.record_stream(self.stream)
+        check(fn(self.ctx, _dev_ptr(dL_dmT, 3 * self.ncell, "dL/dm_T"), int(n), float(dt), int(ckpt_every),
+                 scratch.data_ptr(), nbytes,
+                 None if g_hext is None else _dev_ptr(g_hext, 3 * self.ncell, "g_hext"),
+                 None if g_ms is None else _dev_ptr(g_ms, self.ncell, "g_ms"),
+                 None if gm0 is None else gm0.data_ptr()), name, self.ctx)
         return gm0
 
     def energy(self):
@@ -214,6 +234,14 @@ def _tuned(films, device, options, tuned):
         return dict(options or {})
     from . import autotune
     return autotune.best(films, device)
+
+
+class Tape:
+    """Checkpoints written by ``Grace.step_checkpointed``: the device scratch and the
+    (n, dt, ckpt_every) they were taken with."""
+
+    def __init__(self, scratch: torch.Tensor, nbytes: int, n: int, dt: float, ckpt_every: int):
+        self.scratch, self.nbytes, self.n, self.dt, self.ckpt_every = scratch, nbytes, n, dt, ckpt_every
 
 
 class Grace(_Base):

@@ -56,7 +56,7 @@ def oracle_grads(f, m0, ms, h, target, dt, steps):
 
 
 @pytest.mark.parametrize("grid,steps,ckpt", [((24, 16, 2), 37, 8), ((20, 12, 1), 30, 30),
-                                             ((12, 10, 6), 20, 7)])
+                                             ((12, 10, 6), 20, 7), ((4, 6, 3), 15, 4), ((3, 5, 2), 9, 1)])
 def test_backward_matches_fp64_adjoint(grid, steps, ckpt):
     dt = 1e-14
     f, m0, ms, h, target, g = setup(grid, (4e-9, 4e-9, 3e-9), steps, Ku=2e3)
@@ -187,3 +187,35 @@ def test_backward_graph_replay_equals_direct_launches():
     for a, b in zip(*outs):
         assert torch.equal(a, b)
     assert torch.equal(outs[0][3], dev(m0))          # the state is left at m_0
+
+
+def test_checkpointed_forward_and_backward_equal_the_plain_calls():
+    """grace_step_checkpointed ends at the state grace_step reaches, and the adjoint from its
+    checkpoints (grace_backward_checkpointed) equals grace_backward, which collects the
+    same checkpoints in a forward pass of its own, bit for bit (41 = 3 x 12 + 5 steps)."""
+    dt, steps, ckpt = 1e-14, 41, 12
+    f, m0, ms, h, target, g = setup((24, 16, 2), (4e-9, 4e-9, 3e-9), steps, Ku=2e3)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(DEV)
+    g.set_ms_field(dev(ms))
+    g.set_hext_field(dev(h))
+    g.set_m(dev(m0))
+    tape = g.step_checkpointed(steps, dt, ckpt)
+    m_tape = g.get_m()
+    g.set_m(dev(m0))
+    g.step(steps, dt)
+    assert torch.equal(m_tape, g.get_m())
+    n = 3 * f.ncells
+    lam = torch.linspace(-1e-3, 1e-3, n, device=DEV)
+    outs = []
+    for use_tape in (False, True):
+        g.set_m(dev(m0) if not use_tape else m_tape)
+        gh = torch.zeros(n, device=DEV)
+        gms = torch.zeros(f.ncells, device=DEV)
+        gm0 = g.backward(lam, steps, dt, ckpt, gh, gms, tape=tape if use_tape else None)
+        outs.append((gh, gms, gm0, g.get_m()))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    assert torch.equal(outs[1][3], dev(m0))          # the state is left at m_0
+    with pytest.raises(ValueError):
+        g.backward(lam, steps, dt, ckpt + 1, tape=tape)
+    g.close()

@@ -2,8 +2,8 @@
 shared-memory-extent checks in a workspace word instead of trapping, and every runtime
 buffer is followed by a guard region.  Odd and edge shapes that take every launch path
 (runtime-length x / y / z kernels, the fused and the split compile-time paths, a batch on
-the grouped and the persistent launch, Heun, the adjoint) must leave the word clear and the
-guards intact, and give the release library's results.
+the grouped and the persistent launch, Heun, the adjoint on both x passes) must leave the word clear and the guards intact, and give the
+release library's results.
 
 Each library runs in a subprocess of its own (GRACE_DEBUG selects which one the binding
 loads)."""
@@ -60,14 +60,16 @@ for pers in (0, 1):
     arrays["batch%d" % pers] = b.get_m().cpu().numpy()
     check(b, "batch%d" % pers)
     b.close()
-f, m0 = workloads.small_film((24, 16, 2), seed=9, alpha=0.1)
-g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, tuned=False)
-g.set_m(torch.from_numpy(m0.reshape(-1)).cuda())
-n = 3 * f.ncells
-gm0 = g.backward(torch.linspace(-1e-3, 1e-3, n, device="cuda"), 13, 1e-14, 5,
-                 torch.zeros(n, device="cuda"), torch.zeros(f.ncells, device="cuda"))
-arrays["adjoint"] = gm0.cpu().numpy()
-check(g, "adjoint")
+for grid in [(24, 16, 2), (4, 6, 3)]:
+    f, m0 = workloads.small_film(grid, seed=9, alpha=0.1)
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, tuned=False)
+    g.set_m(torch.from_numpy(m0.reshape(-1)).cuda())
+    n = 3 * f.ncells
+    gm0 = g.backward(torch.linspace(-1e-3, 1e-3, n, device="cuda"), 13, 1e-14, 5,
+                     torch.zeros(n, device="cuda"), torch.zeros(f.ncells, device="cuda"))
+    arrays["adjoint%s" % (grid,)] = gm0.cpu().numpy()
+    check(g, "adjoint%s" % (grid,))
+    g.close()
 np.savez(sys.argv[2], **arrays)
 print(json.dumps(res))
 """
