@@ -78,8 +78,11 @@ enum {
                                  m' = normalise(m + dt (f(m) + f(m*))/2), a higher-order
                                  integrator named as future work in Sec. 6 (two H_eff per step;
                                  grace_backward supports Euler only) */
-  GRACE_OPT_TILE_Z = 7,       /* z-pass blocks of films thicker than four cells: 0 (default)
-                                 256 threads, 1 128 threads; before grace_bind only */
+  GRACE_OPT_TILE_Z = 7,       /* z-pass schedule of films thicker than four cells: 0 (default)
+                                 16 points per thread where the padded z length is 128 (one
+                                 shared-memory exchange per transform), else 256-thread blocks;
+                                 1 / 2: 128- / 256-thread blocks at 8 points per thread; 3: 16
+                                 points per thread (as 0); before grace_bind only */
   GRACE_OPT_SIDE_STREAMS = 8, /* batches: 1 (default) the films' launch groups step side by side
                                  on streams of their own; 0 one after another on the bound stream */
   GRACE_OPT_PERSISTENT = 9,   /* 1: grace_step takes all films and all steps of a call (of a

@@ -1,9 +1,10 @@
 """Autotuner for the launch schedule of a film or an ensemble.
 
 For a given set of films it times each candidate schedule on the real device with CUDA
-events and keeps the fastest.  The candidates are the FFT tiles (x-pass lines per block:
-one line or the larger compiled tile; kx columns per fused y block; z-pass blocks of 256
-or 128 threads, i.e. 16 or 8 columns of a 128-point transform), the batch grouping (the
+events and keeps the fastest.  The candidates are the FFT tiles and schedules (x-pass lines per
+block: one line or the larger compiled tile; kx columns per fused y block; the z pass at 16
+points per thread where the padded z length is 128, or 256- or 128-thread blocks at 8
+points per thread), the batch grouping (the
 launch groups of an ensemble stepping side by side on streams of their own, one after
 another, or all in one persistent cooperative launch) and the steps per captured CUDA graph.
 A single film is timed the way the benchmark steps it — single steps, L2 flushed before
@@ -39,7 +40,7 @@ SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.
 CANDIDATES = {
     _lib.OPT_TILE_X: (0, 1, 2),
     _lib.OPT_TILE_YZ: (0, 1, 2, 4),
-    _lib.OPT_TILE_Z: (0, 1),
+    _lib.OPT_TILE_Z: (0, 1, 2),
     _lib.OPT_SIDE_STREAMS: (1, 0),
     _lib.OPT_PERSISTENT: (0, 1),
     _lib.OPT_GRAPH_STEPS: (8, 16, 32),

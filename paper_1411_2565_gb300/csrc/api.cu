@@ -71,7 +71,7 @@ struct Group {
   bool fused = true;
   int Q = 0, Py = 0, nz = 0, Pz = 0;
   int TY = 1, KPB = 1, RPB = 1, TQ = 1;
-  int ZT = 256;             // threads per z-pass block (split path): 256 or 128
+  int ZT = 256;             // z-pass schedule (split path): 256 or 128 threads, or kZ16
   bool xhelp = false;       // x pass with helper warps (few blocks in flight)
   int units[UK_COUNT] = {0, 0, 0, 0, 0};
   size_t smem_x = 0, smem_yz = 0, smem_y = 0, smem_z = 0;
@@ -89,7 +89,7 @@ struct grace_ctx {
   std::vector<int> film_group;
   long long ncell = 0;
   int tile_x = 0, tile_yz = 0;      // 0 = automatic
-  int tile_z = 0;                   // z-pass blocks: 0 = 256 threads, 1 = 128 threads
+  int tile_z = 0;                   // z pass: 0 auto, 1 / 2: 128 / 256 threads, 3: 16 points a thread
   bool side_streams = true;         // batch groups step side by side on streams of their own
   bool persist = false;             // GRACE_OPT_PERSISTENT: one cooperative launch for all groups
   bool persist_ok = false;          // ... and every group has a persistent tile body
@@ -231,7 +231,8 @@ int plan_group(grace_ctx* c, Group& g) {
     g.xhelp = pick_x_help();
     g.smem_x = fast_x_smem(g.Q, g.TY);
     g.RPB = fast_y_rows(g.Py);
-    g.ZT = c->tile_z == 1 ? 128 : 256;
+    // 16 points per thread where the transform has it (Pz = 128), else 256-thread blocks
+    g.ZT = c->tile_z == 1 ? 128 : c->tile_z == 2 ? 256 : (g.Pz == 128 ? kZ16 : 256);
     g.TQ = fast_z_cols(g.Pz, g.ZT);
     if (g.smem_x > kSmemMax) return GRACE_EUNSUPPORTED;
   } else if (g.fast) {
@@ -1514,7 +1515,7 @@ int grace_set_option(grace_ctx* c, int option, long long value) {
     case GRACE_OPT_TILE_Z: {
       if (c->bound) return fail(c, GRACE_ESTATE, "tile options must be set before grace_bind");
       if (value < 0 || value > 64) return fail(c, GRACE_EINVAL, "tile option out of range 0..64");
-      if (option == GRACE_OPT_TILE_Z && value > 1) return fail(c, GRACE_EINVAL, "GRACE_OPT_TILE_Z takes 0 or 1");
+      if (option == GRACE_OPT_TILE_Z && value > 3) return fail(c, GRACE_EINVAL, "GRACE_OPT_TILE_Z takes 0..3");
       const int old_x = c->tile_x, old_yz = c->tile_yz, old_z = c->tile_z;
       (option == GRACE_OPT_TILE_X ? c->tile_x : option == GRACE_OPT_TILE_YZ ? c->tile_yz : c->tile_z) = (int)value;
       const int st = plan(c);

@@ -183,6 +183,100 @@ __global__ void __launch_bounds__(z_threads(PZ, NT), z_threads(PZ, NT) <= 128 ? 
   }
 }
 
+// z pass for Pz = 128 with 16 points per thread (fft_pk128x16): 8 threads per column, one
+// shared-memory exchange per transform instead of two; 128-thread blocks (16 columns) at
+// 3 per SM (up to 168 registers: the 16 pair points and 16 scalar points of a thread).
+// Same distribution, product and stores as kz_fast, with 8 in place of Pz/8.
+constexpr int kZ16Cols = 16;
+constexpr int kZ16Stride = 129;    // float4 / float2 slots per column: odd, see fft_pk128x16
+
+__global__ void __launch_bounds__(kZ16Cols * 8, 3) kz_fast16(const FilmDev* __restrict__ films, LaunchP lp) {
+  constexpr int PZ = 128, T = 8, TQ = kZ16Cols, NTB = TQ * T, LS = kZ16Stride;
+  const int tid = threadIdx.x;
+  const int qi = tid % TQ, j = tid / TQ;        // q fastest: coalesced global access
+  const int unit = blockIdx.x;
+  const FilmDev& f = films[find_film(films, lp.nfilms, UK_Z, unit)];
+  const int Kz = f.Kz, Ky = f.Ky, nz = f.nz, Py = f.Py, lpy = __ffs(Py) - 1;   // Py: a power of two
+  const int ncol = f.Kx * Py;                    // srow == Py on the split path
+  const int q0 = (unit - f.u0[UK_Z]) * TQ;
+  const int q = q0 + qi;
+  const bool ok = q < ncol;
+  extern __shared__ float4 smem4[];
+  float4* sp = smem4 + qi * LS;                                           // pair (x, y)
+  float2* sc = reinterpret_cast<float2*>(smem4 + TQ * LS) + qi * LS;     // line z
+  GRACE_DSMEM(f, (size_t)TQ * LS * (sizeof(float4) + sizeof(float2)));
+  const size_t zs = (size_t)ncol;                // S[(c * nz + z) * ncol + q]
+  pdl_launch_dependents();
+  if (TQ <= Py / 2) {
+    // the block's tensor points, pulled into L2 before the dependency wait (as kz_fast)
+    const int kx = q0 >> lpy, ky0 = q0 - (kx << lpy), ky1 = ky0 + TQ - 1;
+    int lo = ky0, hi = ky1;
+    if (ky0 >= Py / 2) {
+      lo = Py - ky1;
+      hi = Py - ky0;
+    }
+    const int l0 = lo * 24 / 128, lines = ((hi + 1) * 24 + 127) / 128 - l0;
+    for (int idx = tid; idx < Kz * lines; idx += NTB) {
+      const int kz = idx / lines, l = idx - kz * lines;
+      prefetch_l2(reinterpret_cast<const char*>(f.T + ((size_t)kx * Kz + kz) * Ky * 6) + (l0 + l) * 128);
+    }
+  }
+  pdl_wait();
+  PC p[16];
+  float2 c[16];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int z = j + s * T;
+    float2 a = make_float2(0.f, 0.f), b = a, cz = a;
+    if (ok && z < nz) {
+      a = f.S[(size_t)(0 * nz + z) * zs + q];
+      b = f.S[(size_t)(1 * nz + z) * zs + q];
+      cz = f.S[(size_t)(2 * nz + z) * zs + q];
+    }
+    p[s] = pc_make(a, b);
+    c[s] = cz;
+    p[s + 8] = pc_zero();
+    c[s + 8] = make_float2(0.f, 0.f);
+  }
+  fft_pk128x16<-1, true>(p, c, j, sp, sc, lp.twb);
+  if (ok) {
+    const int kx = q >> lpy, ky = q - (kx << lpy);
+    const bool ylo = ky <= Py / 2;
+    const int kyp = ylo ? ky : Py - ky;
+    const float sy = ylo ? 1.f : -1.f;
+    GRACE_DCHECK(f, kx < f.Kx && kyp < Ky, DBG_T_INDEX);
+    const float* Tq = f.T + ((size_t)kx * Kz * Ky + kyp) * 6;    // T[kx][kz][ky][6]
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      const int kz = j + s * T;
+      const bool zlo = kz <= PZ / 2;
+      const int kzp = zlo ? kz : PZ - kz;
+      const float sz = zlo ? 1.f : -1.f;
+      const float2* tp = reinterpret_cast<const float2*>(Tq + (size_t)kzp * Ky * 6);
+      const float2 t0 = __ldg(tp), t1 = __ldg(tp + 1), t2 = __ldg(tp + 2);   // xx yy | zz xy | xz yz
+      const float nxx = t0.x, nyy = t0.y, nzz = t1.x, nxy = sy * t1.y, nxz = sz * t2.x, nyz = sy * sz * t2.y;
+      const float2 mx = pc_a(p[s]), my = pc_b(p[s]), mz = c[s];
+      const float2 hx = make_float2(nxx * mx.x + nxy * my.x + nxz * mz.x, nxx * mx.y + nxy * my.y + nxz * mz.y);
+      const float2 hy = make_float2(nxy * mx.x + nyy * my.x + nyz * mz.x, nxy * mx.y + nyy * my.y + nyz * mz.y);
+      c[s] = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
+      p[s] = pc_make(hx, hy);
+    }
+  }
+  __syncthreads();   // every thread has read the forward transform's exchange
+  fft_pk128x16<+1, false>(p, c, j, sp, sc, lp.twb);
+  if (ok) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int z = j + s * T;
+      if (z < nz) {
+        f.S[(size_t)(0 * nz + z) * zs + q] = pc_a(p[s]);
+        f.S[(size_t)(1 * nz + z) * zs + q] = pc_b(p[s]);
+        f.S[(size_t)(2 * nz + z) * zs + q] = c[s];
+      }
+    }
+  }
+}
+
 template <int PY>
 cudaError_t y_disp(int dir, const FilmDev* films, const LaunchP& lp, int nunits, int threads, size_t smem,
                    cudaStream_t s, bool attr) {
@@ -245,9 +339,12 @@ bool fast_split_supported(int Py, int Pz) { return Py >= 16 && Py <= 2048 && Pz 
 
 // rows per block (y: two per pair) and columns per z block (zt = 256 or 128 threads)
 int fast_y_rows(int Py) { return 2 * y_pairs(Py); }
-int fast_z_cols(int Pz, int zt) { return z_threads(Pz, zt) / (Pz / 8); }
+int fast_z_cols(int Pz, int zt) {
+  return zt == kZ16 && Pz == 128 ? kZ16Cols : z_threads(Pz, zt) / (Pz / 8);
+}
 size_t fast_y_smem(int Py) { return (size_t)y_pairs(Py) * pk_line_stride(Py) * sizeof(float4); }
 size_t fast_z_smem(int Pz, int zt) {
+  if (zt == kZ16 && Pz == 128) return (size_t)kZ16Cols * kZ16Stride * (sizeof(float4) + sizeof(float2));
   return (size_t)fast_z_cols(Pz, zt) * (pk_line_stride(Pz) * sizeof(float4) + fast_line_stride(Pz, 1) * sizeof(float2));
 }
 
@@ -255,6 +352,9 @@ cudaError_t configure_fast_split(int Py, int Pz) {
   LaunchP lp{};
   cudaError_t e = ydispatch(Py, 0, nullptr, lp, 0, 0, std::max<size_t>(fast_y_smem(Py), 1), nullptr, true);
   if (e == cudaSuccess) e = zdispatch(Pz, nullptr, lp, 0, 0, std::max<size_t>(fast_z_smem(Pz, 256), 1), nullptr, true);
+  if (e == cudaSuccess && Pz == 128)
+    e = cudaFuncSetAttribute((const void*)kz_fast16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fast_z_smem(128, kZ16));
   return e;
 }
 
@@ -265,6 +365,8 @@ cudaError_t launch_fast_y(int Py, int dir, const FilmDev* films, const LaunchP& 
 
 cudaError_t launch_fast_z(int Pz, int zt, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s) {
   if (nunits <= 0) return cudaSuccess;
+  if (zt == kZ16 && Pz == 128)
+    return launch_pdl(kz_fast16, nunits, kZ16Cols * 8, fast_z_smem(128, kZ16), s, films, lp);
   return zdispatch(Pz, films, lp, nunits, z_threads(Pz, zt), fast_z_smem(Pz, zt), s, false);
 }
 

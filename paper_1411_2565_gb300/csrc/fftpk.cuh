@@ -227,4 +227,168 @@ __device__ __forceinline__ void fft_pk(PC (&p)[8], float2 (&c)[8], int j, float4
   fft_pk_stage<L, 1, DIR, true, ZU, NC>(p, c, j, sp, sc, tw);
 }
 
+// ---------------------------------------------------------------------------------------
+// 128-point transform with 16 points per thread (8 threads per line): a radix-16 stage in
+// registers, one exchange, and a radix-8 stage done by each thread for two of the 16
+// radix-8 groups.  Thread j holds points j + 8 s, s = 0..15, of every line before and
+// after (the same distribution as fft_pk with L/16 in place of L/8), so one exchange of
+// the 128 points replaces the two of the 8-points-per-thread transform.  Buffer layout: a
+// line's points in natural order (position 16 j + t written, j + 8 s read); the caller
+// gives consecutive lines odd strides so that the 8 (float4) or 16 (float2) lanes of a
+// shared-memory phase, one line each, fall on distinct banks.
+
+// W16^T = exp(DIR 2 pi i T / 16), T = 1..7
+template <int DIR, int T>
+__device__ __forceinline__ float2 w16() {
+  constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, r = 0.70710678118654752440f;
+  constexpr float cs = T == 1 ? c1 : T == 2 ? r : T == 3 ? s1 : T == 4 ? 0.f : T == 5 ? -s1 : T == 6 ? -r : -c1;
+  constexpr float sn = T == 1 ? s1 : T == 2 ? r : T == 3 ? c1 : T == 4 ? 1.f : T == 5 ? c1 : T == 6 ? r : s1;
+  return make_float2(cs, DIR < 0 ? -sn : sn);
+}
+
+template <int DIR, int T>
+__device__ __forceinline__ void pbfly16(PC& e, PC& o) {
+  PC ot = o;
+  if constexpr (T == 4) {
+    PC a, b;
+    pbfly_i<DIR>(e, o, a, b);
+    e = a;
+    o = b;
+    return;
+  } else if constexpr (T > 0) {
+    ot = pcmul(o, w16<DIR, T>());
+  }
+  const PC a = padd(e, ot), b = psub(e, ot);
+  e = a;
+  o = b;
+}
+
+template <int DIR, int T>
+__device__ __forceinline__ void bfly16(float2& e, float2& o) {
+  float2 ot = o;
+  if constexpr (T == 4) ot = mul_w4<DIR>(o);
+  else if constexpr (T > 0) ot = cmul(o, w16<DIR, T>());
+  const float2 a = cadd(e, ot), b = csub(e, ot);
+  e = a;
+  o = b;
+}
+
+// 16-point DFT, natural order in and out (even / odd halves as two 8-point DFTs); ZU:
+// inputs 8..15 are zero
+template <int DIR, bool ZU>
+__device__ __forceinline__ void pdft16(PC* v) {
+  PC e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  if constexpr (ZU) {
+    pdft8_upper_zero<DIR>(e);
+    pdft8_upper_zero<DIR>(o);
+  } else {
+    pdft8<DIR>(e);
+    pdft8<DIR>(o);
+  }
+  pbfly16<DIR, 0>(e[0], o[0]);
+  pbfly16<DIR, 1>(e[1], o[1]);
+  pbfly16<DIR, 2>(e[2], o[2]);
+  pbfly16<DIR, 3>(e[3], o[3]);
+  pbfly16<DIR, 4>(e[4], o[4]);
+  pbfly16<DIR, 5>(e[5], o[5]);
+  pbfly16<DIR, 6>(e[6], o[6]);
+  pbfly16<DIR, 7>(e[7], o[7]);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    v[t] = e[t];
+    v[t + 8] = o[t];
+  }
+}
+
+template <int DIR, bool ZU>
+__device__ __forceinline__ void dft16(float2* v) {
+  float2 e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  if constexpr (ZU) {
+    dft8_upper_zero<DIR>(e);
+    dft8_upper_zero<DIR>(o);
+  } else {
+    dft8<DIR>(e);
+    dft8<DIR>(o);
+  }
+  bfly16<DIR, 0>(e[0], o[0]);
+  bfly16<DIR, 1>(e[1], o[1]);
+  bfly16<DIR, 2>(e[2], o[2]);
+  bfly16<DIR, 3>(e[3], o[3]);
+  bfly16<DIR, 4>(e[4], o[4]);
+  bfly16<DIR, 5>(e[5], o[5]);
+  bfly16<DIR, 6>(e[6], o[6]);
+  bfly16<DIR, 7>(e[7], o[7]);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    v[t] = e[t];
+    v[t + 8] = o[t];
+  }
+}
+
+// Radix-8 stage (NS = 16, the last one) of a 128-point line on the 8 points jv + 16 r of
+// radix-8 group jv: twiddles W128^(r jv), then an 8-point DFT; outputs X[jv + 16 r]
+template <int DIR, int NC>
+__device__ __forceinline__ void pk128_stage8(PC* p, float2* c, int jv, const float2* __restrict__ tw) {
+  const float2 w1 = twb_at<DIR>(tw, 128, jv), w2 = twb_at<DIR>(tw, 64, jv), w4 = twb_at<DIR>(tw, 32, jv);
+  const float2 w3 = cmul(w1, w2);
+  const float2 w[8] = {w1, w1, w2, w3, w4, cmul(w1, w4), cmul(w2, w4), cmul(w3, w4)};
+#pragma unroll
+  for (int r = 1; r < 8; ++r) {
+    p[r] = pcmul(p[r], w[r]);
+    if constexpr (NC > 0) c[r] = cmul(c[r], w[r]);
+  }
+  pdft8<DIR>(p);
+  if constexpr (NC > 0) dft8<DIR>(c);
+}
+
+// The pair p and (NC = 1) the scalar line c, 128 points, thread j (0..7) holding points
+// j + 8 s; ZU: inputs 64..127 zero.  One exchange (two barriers' worth: the caller syncs
+// before the buffers are written again).
+template <int DIR, bool ZU, int NC = 1>
+__device__ __forceinline__ void fft_pk128x16(PC (&p)[16], float2 (&c)[16], int j, float4* sp, float2* sc,
+                                             const float2* __restrict__ tw) {
+  pdft16<DIR, ZU>(p);
+  if constexpr (NC > 0) dft16<DIR, ZU>(c);
+  // radix-16 output t of thread j is point 16 j + t of the half-transformed line
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    sp[16 * j + t] = make_float4(p[t].r.x, p[t].r.y, p[t].i.x, p[t].i.y);
+    if constexpr (NC > 0) sc[16 * j + t] = c[t];
+  }
+  __syncthreads();
+  // points j + 8 s: s even -> group j (its points j + 16 r), s odd -> group j + 8
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const float4 q = sp[j + 8 * s];
+    p[s] = {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+    if constexpr (NC > 0) c[s] = sc[j + 8 * s];
+  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    PC pb[8];
+    float2 cb[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      pb[r] = p[2 * r + b];
+      if constexpr (NC > 0) cb[r] = c[2 * r + b];
+    }
+    pk128_stage8<DIR, NC>(pb, cb, j + 8 * b, tw);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      p[2 * r + b] = pb[r];
+      if constexpr (NC > 0) c[2 * r + b] = cb[r];
+    }
+  }
+}
+
 }  // namespace grace

@@ -179,7 +179,10 @@ cudaError_t launch_fast_yz(int Py, int nz, const FilmDev* films, const LaunchP& 
 cudaError_t configure_kernels(size_t smem_x, size_t smem_yz, size_t smem_y, size_t smem_z);
 bool fast_split_supported(int Py, int Pz);
 int fast_y_rows(int Py);
-int fast_z_cols(int Pz, int zt);   // zt: z-pass block threads, 256 or 128
+// zt: z-pass schedule: 256 or 128 threads per block at 8 points per thread, or kZ16: 16
+// points per thread (Pz = 128 only, one exchange per transform)
+constexpr int kZ16 = 16;
+int fast_z_cols(int Pz, int zt);
 cudaError_t configure_fast_split(int Py, int Pz);
 cudaError_t launch_fast_y(int Py, int dir, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s);
 cudaError_t launch_fast_z(int Pz, int zt, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s);

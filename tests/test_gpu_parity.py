@@ -56,7 +56,7 @@ def make(f, m0, ms=None, hfield=None):
 
 
 GRIDS = [(24, 12, 2), (17, 5, 3), (1, 1, 1), (3, 1, 1), (1, 7, 1), (2, 2, 2), (8, 8, 1), (9, 3, 6), (5, 2, 7),
-         (40, 20, 4), (16, 8, 6), (33, 9, 5), (5, 40, 1), (64, 3, 2), (130, 6, 1)]
+         (40, 20, 4), (16, 8, 6), (33, 9, 5), (5, 40, 1), (64, 3, 2), (130, 6, 1), (7, 9, 33), (12, 10, 64)]
 
 
 @pytest.mark.parametrize("grid", GRIDS)
@@ -72,6 +72,26 @@ def test_heff_matches_oracle(grid, mask):
     # the state and the spectrum are unchanged by heff: a second call agrees bit for bit
     h2 = g.heff(mask).cpu().numpy().reshape(m0.shape)
     assert np.array_equal(h, h2)
+
+
+# the z-pass schedules of a padded z length of 128 (16 points per thread, the default there;
+# 128- and 256-thread blocks at 8 points per thread), ragged in every axis
+@pytest.mark.parametrize("tile_z", [0, 1, 2, 3])
+def test_z_schedules_match_oracle(tile_z):
+    Grace, _ = _grace()
+    grid = (11, 13, 41)
+    f, m0 = workloads.small_film(grid, cell=(3.5e-9, 2.5e-9, 3e-9), seed=23, Ku=2e4, hext=(1.5e4, -2e4, 3e3))
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=DEV, options={_lib.OPT_TILE_Z: tile_z})
+    g.set_hext(f.hext)
+    g.set_m(torch.from_numpy(m0.reshape(-1)).to(DEV))
+    p = params(f)
+    D = llg.Demag(grid, f.cell)
+    h = g.heff().cpu().numpy().reshape(m0.shape)
+    assert np.abs(h - llg.heff(m0, p, D)).max() / f.Ms <= TOL_H
+    g.step(1, 2e-14)
+    m1 = g.get_m().cpu().numpy().reshape(m0.shape)
+    assert np.abs(m1 - llg.euler_step(m0, p, 2e-14, D)).max() <= 2e-6
+    g.close()
 
 
 # the largest axis (2048 cells, padded length 4096) on each path: 2048-point compile-time
