@@ -219,3 +219,31 @@ def test_checkpointed_forward_and_backward_equal_the_plain_calls():
     with pytest.raises(ValueError):
         g.backward(lam, steps, dt, ckpt + 1, tape=tape)
     g.close()
+
+
+@pytest.mark.parametrize("tile_x", [1, 2])
+def test_backward_on_the_x_tiles_of_px_512(tile_x):
+    """The adjoint x-pass modes on one line per block (with helper warps) and on the 4-line
+    tile (Px = 512), against the FP64 adjoint."""
+    from paper_1411_2565_gb300 import _lib
+    from paper_1411_2565_gb300.grace import Grace
+    dt, steps, ckpt = 1e-14, 11, 4
+    f, m0, ms, h, target, g0 = setup((140, 9, 2), (4e-9, 4e-9, 3e-9), steps, Ku=2e3)
+    g0.close()
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=DEV, options={_lib.OPT_TILE_X: tile_x})
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(DEV)
+    g.set_ms_field(dev(ms))
+    g.set_hext_field(dev(h))
+    g.set_m(dev(m0))
+    tape = g.step_checkpointed(steps, dt, ckpt)
+    mT = g.get_m()
+    n = mT.numel() // 3
+    lamT = 2.0 * (mT - dev(target)) / n
+    gh = torch.zeros(3 * n, device=DEV)
+    gms = torch.zeros(n, device=DEV)
+    gm0 = g.backward(lamT, steps, dt, ckpt, gh, gms, tape=tape)
+    loss, o_m0, o_h, o_ms = oracle_grads(f, m0, ms, h, target, dt, steps)
+    assert rel(gh.cpu().numpy(), o_h) <= 1e-3
+    assert rel(gms.cpu().numpy(), o_ms) <= 1e-3
+    assert rel(gm0.cpu().numpy(), o_m0) <= 1e-3
+    g.close()

@@ -94,6 +94,27 @@ def test_z_schedules_match_oracle(tile_z):
     g.close()
 
 
+# the x-pass tiles of Px = 512 (automatic, one line per block, four lines per block), on the
+# fused and the split path, ragged in y
+@pytest.mark.parametrize("grid", [(150, 21, 3), (131, 17, 6)])
+@pytest.mark.parametrize("tile_x", [0, 1, 2])
+def test_x_tiles_match_oracle(grid, tile_x):
+    Grace, _ = _grace()
+    f, m0 = workloads.small_film(grid, cell=(3.5e-9, 2.5e-9, 3e-9), seed=29, Ku=2e4, hext=(1.5e4, -2e4, 3e3))
+    g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, device=DEV, options={_lib.OPT_TILE_X: tile_x})
+    g.set_hext(f.hext)
+    g.set_m(torch.from_numpy(m0.reshape(-1)).to(DEV))
+    p = params(f)
+    D = llg.Demag(grid, f.cell)
+    for mask in (1, 15):
+        h = g.heff(mask).cpu().numpy().reshape(m0.shape)
+        assert np.abs(h - llg.heff(m0, p, D, mask=mask)).max() / f.Ms <= TOL_H, mask
+    g.step(1, 2e-14)
+    m1 = g.get_m().cpu().numpy().reshape(m0.shape)
+    assert np.abs(m1 - llg.euler_step(m0, p, 2e-14, D)).max() <= 2e-6
+    g.close()
+
+
 # the largest axis (2048 cells, padded length 4096) on each path: 2048-point compile-time
 # x lines, 1024-row fused y pass (Py = 2048), 2048-point compile-time z pass (Pz = 2048),
 # and the runtime-length kernels at length 4096 along y and z
