@@ -47,9 +47,11 @@ typedef enum {
   GRACE_EWORKSPACE = -2,   /* workspace smaller than grace_workspace_size or misaligned */
   GRACE_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
   GRACE_ETIMEOUT = -4,     /* a bounded device-side wait expired: a grid barrier of the
-                              persistent batch launch (GRACE_OPT_PERSISTENT) waited longer
-                              than GRACE_OPT_BARRIER_TIMEOUT_US; reported by the next
-                              synchronising call (grace_sync, grace_energy, grace_get_m_host) */
+                              persistent batch launch (GRACE_OPT_PERSISTENT), or the wait of
+                              the staged z pass (GRACE_OPT_TILE_Z = 4) for a tensor copy,
+                              took longer than GRACE_OPT_BARRIER_TIMEOUT_US; reported by the
+                              next synchronising call (grace_sync, grace_energy,
+                              grace_get_m_host) */
   GRACE_ESTATE = -5,       /* call out of order (e.g. step before bind / set_m) */
   GRACE_ENONFINITE = -6,   /* a NaN or Inf appeared in <m> (checked by grace_energy) */
   GRACE_EUNSUPPORTED = -7  /* valid arguments outside what this build supports */
@@ -82,7 +84,13 @@ enum {
                                  16 points per thread where the padded z length is 128 (one
                                  shared-memory exchange per transform), else 256-thread blocks;
                                  1 / 2: 128- / 256-thread blocks at 8 points per thread; 3: 16
-                                 points per thread (as 0); before grace_bind only */
+                                 points per thread (as 0); 4: as 3 for a single film, as a
+                                 persistent kernel whose blocks stage the next tile's spectrum
+                                 columns into shared memory with one TMA tensor copy each
+                                 (cp.async.bulk.tensor, bounded mbarrier wait) while they
+                                 transform the current one; same results bit for bit, slower
+                                 on the 256x256x64 block (it leaves L1 little room); as 0 for
+                                 other shapes and for batches; before grace_bind only */
   GRACE_OPT_SIDE_STREAMS = 8, /* batches: 1 (default) the films' launch groups step side by side
                                  on streams of their own; 0 one after another on the bound stream */
   GRACE_OPT_PERSISTENT = 9,   /* 1: grace_step takes all films and all steps of a call (of a
@@ -92,11 +100,14 @@ enum {
                                  four cells in z with 64 <= Px/2 <= 1024 and 16 <= Py <= 512;
                                  otherwise, and for traced steps, the grouped launches run).
                                  0 (default): grouped launches.  Before grace_bind only */
-  GRACE_OPT_BARRIER_TIMEOUT_US = 10, /* bound of each grid-barrier wait of the persistent launch,
-                                 microseconds (1e3..6e7, default 1e6) */
+  GRACE_OPT_BARRIER_TIMEOUT_US = 10, /* bound of each grid-barrier wait of the persistent launch
+                                 and of each copy wait of the staged z pass, microseconds
+                                 (1e3..6e7, default 1e6) */
   GRACE_OPT_TEST_SKIP_ARRIVE = 11 /* failure-detection test hook: block `value` of the persistent
                                  launch skips its first barrier arrival, so every wait runs out
-                                 and the launch ends with GRACE_ETIMEOUT; -1 (default) off */
+                                 and the launch ends with GRACE_ETIMEOUT; block `value` of the
+                                 staged z pass skips its first copy, so its wait runs out (the
+                                 same report); -1 (default) off */
 };
 
 /* Kernel kinds reported by grace_trace_read. */
@@ -213,7 +224,8 @@ int grace_step(grace_ctx *ctx, int n, double dt_s);
 
 /* grace_sync - synchronise the bound stream; GRACE_ETIMEOUT if a persistent launch since the
  * last report had a grid barrier time out (the state is then that of the last completed
- * step phase; the barrier words are cleared, so later steps run again). */
+ * step phase; the barrier words are cleared, so later steps run again), or a block of the
+ * staged z pass gave up waiting for its copy (the state after that step is not valid). */
 int grace_sync(grace_ctx *ctx);
 
 /*

@@ -40,7 +40,7 @@ SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.
 CANDIDATES = {
     _lib.OPT_TILE_X: (0, 1, 2),
     _lib.OPT_TILE_YZ: (0, 1, 2, 4),
-    _lib.OPT_TILE_Z: (0, 1, 2),
+    _lib.OPT_TILE_Z: (0, 1, 2, 4),
     _lib.OPT_SIDE_STREAMS: (1, 0),
     _lib.OPT_PERSISTENT: (0, 1),
     _lib.OPT_GRAPH_STEPS: (8, 16, 32),

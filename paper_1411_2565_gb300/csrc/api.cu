@@ -71,7 +71,8 @@ struct Group {
   bool fused = true;
   int Q = 0, Py = 0, nz = 0, Pz = 0;
   int TY = 1, KPB = 1, RPB = 1, TQ = 1;
-  int ZT = 256;             // z-pass schedule (split path): 256 or 128 threads, or kZ16
+  int ZT = 256;             // z-pass schedule (split path): 256 or 128 threads, kZ16 or kZ16T
+  ZMap zmap{};              // kZ16T: tensor map of the film's S (made at bind)
   bool xhelp = false;       // x pass with helper warps (few blocks in flight)
   int units[UK_COUNT] = {0, 0, 0, 0, 0};
   size_t smem_x = 0, smem_yz = 0, smem_y = 0, smem_z = 0;
@@ -118,6 +119,7 @@ struct grace_ctx {
   bool pulse = false;               // applied field scaled by a trapezoid envelope
   double pulse_t[3] = {0.0, 0.0, 0.0};
   int graph_steps = 16;
+  int nsm = 0;                      // SMs of the device (sm_count() at planning)
   cudaStream_t cap = nullptr;
   std::vector<cudaStream_t> aux;    // one per group past the first: groups step side by side
   std::vector<cudaEvent_t> aux_join;
@@ -232,7 +234,10 @@ int plan_group(grace_ctx* c, Group& g) {
     g.smem_x = fast_x_smem(g.Q, g.TY);
     g.RPB = fast_y_rows(g.Py);
     // 16 points per thread where the transform has it (Pz = 128), else 256-thread blocks
-    g.ZT = c->tile_z == 1 ? 128 : c->tile_z == 2 ? 256 : (g.Pz == 128 ? kZ16 : 256);
+    // staged (TMA) form for a single film, where the whole column fits one copy box
+    const bool staged = g.Pz == 128 && g.idx.size() == 1 && 3 * g.nz <= 256;
+    g.ZT = c->tile_z == 1 ? 128 : c->tile_z == 2 ? 256 : c->tile_z == 4 && staged ? kZ16T
+                                                     : (g.Pz == 128 ? kZ16 : 256);
     g.TQ = fast_z_cols(g.Pz, g.ZT);
     if (g.smem_x > kSmemMax) return GRACE_EUNSUPPORTED;
   } else if (g.fast) {
@@ -295,6 +300,7 @@ int plan_group(grace_ctx* c, Group& g) {
 
 // Choose groups, kernels, tile sizes, unit counts and the workspace layout.
 int plan(grace_ctx* c) {
+  c->nsm = sm_count();
   c->classes.clear();
   c->groups.clear();
   // shape classes (films with identical grid and cell share one tensor)
@@ -558,6 +564,10 @@ LaunchP group_lp(const grace_ctx* c, const Group& g) {
   lp.tw = lp.twb + (GRACE_LMAX - 2);   // the base-GRACE_LMAX table
   lp.pdl = c->pdl ? 1 : 0;
   lp.xhelp = g.xhelp ? 1 : 0;
+  lp.nsm = c->nsm;
+  lp.status = &reinterpret_cast<PersistSync*>(c->ws + c->o_psync)->status;
+  lp.limit_ns = (unsigned long long)c->barrier_timeout_us * 1000ull;
+  lp.skip_copy_block = c->skip_arrive;
   lp.k1 = reinterpret_cast<float*>(c->ws + c->o_run + c->o_k1);
   lp.hscale = c->pulse ? time_scale(c) : nullptr;
   return lp;
@@ -593,7 +603,10 @@ cudaError_t enqueue_conv(grace_ctx* c, const Group& g, const LaunchP& lp, cudaSt
   const FilmDev* f = gfilms(c, g);
   if (g.split_fast) {
     GRACE_LAUNCH(c, TK_Y_FAST, s, launch_fast_y(g.Py, -1, f, lp, g.units[UK_Y], s));
-    GRACE_LAUNCH(c, TK_Z_FAST, s, launch_fast_z(g.Pz, g.ZT, f, lp, g.units[UK_Z], s));
+    if (g.ZT == kZ16T)
+      GRACE_LAUNCH(c, TK_Z_FAST, s, launch_fast_z_tma(f, lp, g.units[UK_Z], g.nz, &g.zmap, s));
+    else
+      GRACE_LAUNCH(c, TK_Z_FAST, s, launch_fast_z(g.Pz, g.ZT, f, lp, g.units[UK_Z], s));
     GRACE_LAUNCH(c, TK_Y_FAST, s, launch_fast_y(g.Py, +1, f, lp, g.units[UK_Y], s));
     return cudaSuccess;
   }
@@ -783,17 +796,23 @@ void drop_graphs(grace_ctx* c) {
   }
 }
 
+bool uses_staged_z(const grace_ctx* c) {
+  for (const auto& g : c->groups)
+    if (g.ZT == kZ16T) return true;
+  return false;
+}
+
 // After a stream synchronisation: a persistent launch whose grid barrier timed out left
 // GRACE_ETIMEOUT in the status word; report it once and clear the barrier words.
 int persist_status(grace_ctx* c) {
-  if (!c->persist_ok) return GRACE_OK;
+  if (!c->persist_ok && !uses_staged_z(c)) return GRACE_OK;
   PersistSync h{};
   GRACE_CUDA(c, cudaMemcpy(&h, c->ws + c->o_psync, sizeof h, cudaMemcpyDeviceToHost));
   if (h.status == 0) return GRACE_OK;
   GRACE_CUDA(c, cudaMemsetAsync(c->ws + c->o_psync, 0, sizeof(PersistSync), c->stream));
   GRACE_CUDA(c, cudaStreamSynchronize(c->stream));
-  return fail(c, GRACE_ETIMEOUT, "a grid barrier of the persistent batch launch timed out; the steps "
-                                 "after it were not taken");
+  return fail(c, GRACE_ETIMEOUT, "a bounded wait timed out (a grid barrier of the persistent batch launch or "
+                                 "a staged copy of the z pass); the results of the steps since are not valid");
 }
 
 int ready(grace_ctx* c, bool need_m) {
@@ -936,6 +955,12 @@ int grace_bind(grace_ctx* c, void* dev_ws, size_t bytes, void* cuda_stream) {
   fill_pointers(c);
   int st = upload_films(c);
   if (st != GRACE_OK) return st;
+  for (auto& g : c->groups) {
+    if (g.ZT != kZ16T) continue;
+    const FilmDev& d = c->fd[g.idx[0]];
+    GRACE_CUDA(c, make_z_map(&g.zmap, d.S, d.Kx * d.Py, 3 * d.nz));
+  }
+  if (uses_staged_z(c)) GRACE_CUDA(c, cudaMemsetAsync(c->ws + c->o_psync, 0, sizeof(PersistSync), c->stream));
   if (c->persist_ok) {
     // the persistent kernel's work list (groups in order, tiles numbered across groups),
     // its barrier words cleared, and its grid: every block co-resident
@@ -1515,7 +1540,7 @@ int grace_set_option(grace_ctx* c, int option, long long value) {
     case GRACE_OPT_TILE_Z: {
       if (c->bound) return fail(c, GRACE_ESTATE, "tile options must be set before grace_bind");
       if (value < 0 || value > 64) return fail(c, GRACE_EINVAL, "tile option out of range 0..64");
-      if (option == GRACE_OPT_TILE_Z && value > 3) return fail(c, GRACE_EINVAL, "GRACE_OPT_TILE_Z takes 0..3");
+      if (option == GRACE_OPT_TILE_Z && value > 4) return fail(c, GRACE_EINVAL, "GRACE_OPT_TILE_Z takes 0..4");
       const int old_x = c->tile_x, old_yz = c->tile_yz, old_z = c->tile_z;
       (option == GRACE_OPT_TILE_X ? c->tile_x : option == GRACE_OPT_TILE_YZ ? c->tile_yz : c->tile_z) = (int)value;
       const int st = plan(c);

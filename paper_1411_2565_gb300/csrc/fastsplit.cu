@@ -10,6 +10,8 @@
 //   with parities: xy odd in ky, xz odd in kz, yz odd in both) is local to the thread,
 //   its six tensor values in three 8-byte loads (T[kx][kz][ky][6]); the inverse z FFT
 //   keeps nz outputs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,6 +55,21 @@ __global__ void __launch_bounds__(y_threads(PY), y_min_blocks(PY))
   float2* __restrict__ S1 = f.S + (size_t)(ok1 ? row + 1 : 0) * f.srow;
   pdl_launch_dependents();
   pdl_wait();
+  {
+    // this pair's rows one wave later (y_min_blocks(PY) blocks on each SM): into L2 now, so
+    // that the block starting then waits for L2 rather than DRAM.  Rows 2p, 2p + 1 are
+    // adjacent in S; the forward pass reads the first ny values of each, the inverse all Py.
+    const int rown = row + 2 * RPP * y_min_blocks(PY) * lp.nsm;
+    if (lp.nsm > 0 && rown + 1 < rows) {
+      constexpr int kLine = 128 / (int)sizeof(float2);   // values per 128-byte line
+      const int lines = ((DIR < 0 ? ny : PY) + kLine - 1) / kLine;
+      const float2* Sn = f.S + (size_t)rown * f.srow;
+      for (int l = j; l < 2 * lines; l += T) {
+        const int r = l / lines;
+        prefetch_l2(Sn + (size_t)r * f.srow + (l - r * lines) * kLine);
+      }
+    }
+  }
   PC p[8];
   float2 unused[8];
   const float2 zero = make_float2(0.f, 0.f);
@@ -222,6 +239,14 @@ __global__ void __launch_bounds__(kZ16Cols * 8, 3) kz_fast16(const FilmDev* __re
     }
   }
   pdl_wait();
+  {
+    // the spectrum lines of the block one wave later (3 blocks on each SM): into L2 now, so
+    // that its loads wait for L2 rather than DRAM; TQ columns of 8 bytes are one 128-byte
+    // line per (c, z) row
+    const int qn = q0 + 3 * lp.nsm * TQ;
+    if (lp.nsm > 0 && qn < ncol)
+      for (int idx = tid; idx < 3 * nz; idx += NTB) prefetch_l2(f.S + (size_t)idx * zs + qn);
+  }
   PC p[16];
   float2 c[16];
 #pragma unroll
@@ -274,6 +299,206 @@ __global__ void __launch_bounds__(kZ16Cols * 8, 3) kz_fast16(const FilmDev* __re
         f.S[(size_t)(2 * nz + z) * zs + q] = c[s];
       }
     }
+  }
+}
+
+// ---- the z pass with TMA-staged spectrum columns (kZ16T) ----
+//
+// A persistent form of kz_fast16 for one film: each block walks tiles blockIdx.x,
+// + gridDim.x, ... (TQ = 16 columns each) and keeps the next tile's spectrum in flight
+// while it transforms the current one.  Tile t's input, S[c][z][16 t .. 16 t + 15] for the
+// 3 nz rows (c, z), is one box of the film's tensor map: thread 0 arms the block's
+// mbarrier with the box's byte count and issues one cp.async.bulk.tensor copy into the
+// stage buffer; after the wait every thread takes its 3 x 8 points from there, the block
+// syncs, and thread 0 issues the copy of the tile one grid later into the same buffer, so
+// the DRAM latency of the next tile overlaps this tile's transforms, product and stores.
+// Blocks started together otherwise stay in step and wait on their loads together.
+//
+// The wait is bounded: thread 0 polls the mbarrier against %globaltimer for lp.limit_ns;
+// on expiry it writes GRACE_ETIMEOUT to the workspace status word, waits once more (with
+// the same bound) for its copy in flight, and the block returns.  lp.skip_copy_block makes
+// that block skip its first copy (the failure-detection test hook: its wait runs out).
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make the initialised mbarrier visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// true once phase `parity` of the mbarrier has completed; false after limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+// 2-D tiled tensor copy global -> shared (box at columns x, rows y), completion counted in
+// bytes on the mbarrier
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr int kZTThreads = kZ16Cols * 8;
+// shared memory: the stage (3 nz rows of kZ16Cols values), the exchange buffers of
+// kz_fast16, the mbarrier
+__host__ __device__ constexpr size_t zt_stage_bytes(int nz) { return (size_t)3 * nz * kZ16Cols * sizeof(float2); }
+__host__ __device__ constexpr size_t zt_smem(int nz) {
+  return zt_stage_bytes(nz) + (size_t)kZ16Cols * kZ16Stride * (sizeof(float4) + sizeof(float2)) + 16;
+}
+
+// the 128-byte lines of tensor points that the columns q0 .. q0 + TQ - 1 read (T[kx][kz][ky][6])
+__device__ __forceinline__ void prefetch_tensor_cols(const FilmDev& f, int q0, int TQ, int lpy, int tid, int nt) {
+  const int Kz = f.Kz, Ky = f.Ky, Py = f.Py;
+  if (TQ > Py / 2) return;   // the columns must share kx and one run of |ky|
+  const int kx = q0 >> lpy, ky0 = q0 - (kx << lpy), ky1 = ky0 + TQ - 1;
+  int lo = ky0, hi = ky1;
+  if (ky0 >= Py / 2) {
+    lo = Py - ky1;
+    hi = Py - ky0;
+  }
+  const int l0 = lo * 24 / 128, lines = ((hi + 1) * 24 + 127) / 128 - l0;
+  for (int idx = tid; idx < Kz * lines; idx += nt) {
+    const int kz = idx / lines, l = idx - kz * lines;
+    prefetch_l2(reinterpret_cast<const char*>(f.T + ((size_t)kx * Kz + kz) * Ky * 6) + (l0 + l) * 128);
+  }
+}
+
+__global__ void __launch_bounds__(kZTThreads, 3)
+    kz_tma16(const FilmDev* __restrict__ films, LaunchP lp, const __grid_constant__ CUtensorMap smap) {
+  constexpr int PZ = 128, T = 8, TQ = kZ16Cols, NTB = kZTThreads, LS = kZ16Stride;
+  const int tid = threadIdx.x;
+  const int qi = tid % TQ, j = tid / TQ;        // q fastest, as kz_fast16
+  const FilmDev& f = films[0];                   // one film: the tensor map describes its S
+  const int Kz = f.Kz, Ky = f.Ky, nz = f.nz, Py = f.Py, lpy = __ffs(Py) - 1;   // Py: a power of two
+  const int ncol = f.Kx * Py;                    // a multiple of TQ (Py >= 16)
+  const int ntiles = ncol / TQ;
+  const size_t zs = (size_t)ncol;                // S[(c * nz + z) * ncol + q]
+  extern __shared__ __align__(128) float4 smem4[];
+  const float2* stage = reinterpret_cast<const float2*>(smem4);               // [3 nz][TQ]
+  float4* xb = smem4 + zt_stage_bytes(nz) / sizeof(float4);
+  float4* sp = xb + qi * LS;                                                    // pair (x, y)
+  float2* sc = reinterpret_cast<float2*>(xb + TQ * LS) + qi * LS;              // line z
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(smem4) + zt_smem(nz) - 16);
+  __shared__ int s_ok;
+  GRACE_DSMEM(f, zt_smem(nz));
+  const unsigned box_bytes = (unsigned)zt_stage_bytes(nz);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  pdl_launch_dependents();
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch_tensor_cols(f, tile * TQ, TQ, lpy, tid, NTB);
+  pdl_wait();
+  if (tid == 0 && tile < ntiles && (int)blockIdx.x != lp.skip_copy_block) {
+    mbar_arrive_expect_tx(bar, box_bytes);
+    tma_load_2d(smem4, &smap, bar, tile * TQ, 0);
+  }
+  unsigned parity = 0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    if (tid == 0) {
+      const bool ok = mbar_wait_bounded(bar, parity, lp.limit_ns);
+      if (!ok) {
+        atomicExch(lp.status, -4);   // GRACE_ETIMEOUT
+        mbar_wait_bounded(bar, parity, lp.limit_ns);   // the copy in flight, if any
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    // the phase is complete: every thread observes it before reading the stage
+    for (int it = 0; it < 64 && !mbar_try_wait(bar, parity); ++it) {
+    }
+    parity ^= 1u;
+    const int q0 = tile * TQ, q = q0 + qi;
+    PC p[16];
+    float2 c[16];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int z = j + s * T;
+      float2 a = make_float2(0.f, 0.f), b = a, cz = a;
+      if (z < nz) {
+        a = stage[(0 * nz + z) * TQ + qi];
+        b = stage[(1 * nz + z) * TQ + qi];
+        cz = stage[(2 * nz + z) * TQ + qi];
+      }
+      p[s] = pc_make(a, b);
+      c[s] = cz;
+      p[s + 8] = pc_zero();
+      c[s + 8] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();   // every thread holds its points: the stage takes the next tile
+    const int next = tile + (int)gridDim.x;
+    if (next < ntiles) {
+      prefetch_tensor_cols(f, next * TQ, TQ, lpy, tid, NTB);
+      if (tid == 0) {
+        mbar_arrive_expect_tx(bar, box_bytes);
+        tma_load_2d(smem4, &smap, bar, next * TQ, 0);
+      }
+    }
+    fft_pk128x16<-1, true>(p, c, j, sp, sc, lp.twb);
+    {
+      const int kx = q >> lpy, ky = q - (kx << lpy);
+      const bool ylo = ky <= Py / 2;
+      const int kyp = ylo ? ky : Py - ky;
+      const float sy = ylo ? 1.f : -1.f;
+      GRACE_DCHECK(f, kx < f.Kx && kyp < Ky, DBG_T_INDEX);
+      const float* Tq = f.T + ((size_t)kx * Kz * Ky + kyp) * 6;    // T[kx][kz][ky][6]
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        const int kz = j + s * T;
+        const bool zlo = kz <= PZ / 2;
+        const int kzp = zlo ? kz : PZ - kz;
+        const float sz = zlo ? 1.f : -1.f;
+        const float2* tp = reinterpret_cast<const float2*>(Tq + (size_t)kzp * Ky * 6);
+        const float2 t0 = __ldg(tp), t1 = __ldg(tp + 1), t2 = __ldg(tp + 2);   // xx yy | zz xy | xz yz
+        const float nxx = t0.x, nyy = t0.y, nzz = t1.x, nxy = sy * t1.y, nxz = sz * t2.x, nyz = sy * sz * t2.y;
+        const float2 mx = pc_a(p[s]), my = pc_b(p[s]), mz = c[s];
+        const float2 hx = make_float2(nxx * mx.x + nxy * my.x + nxz * mz.x, nxx * mx.y + nxy * my.y + nxz * mz.y);
+        const float2 hy = make_float2(nxy * mx.x + nyy * my.x + nyz * mz.x, nxy * mx.y + nyy * my.y + nyz * mz.y);
+        c[s] = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
+        p[s] = pc_make(hx, hy);
+      }
+    }
+    __syncthreads();   // every thread has read the forward transform's exchange
+    fft_pk128x16<+1, false>(p, c, j, sp, sc, lp.twb);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int z = j + s * T;
+      if (z < nz) {
+        f.S[(size_t)(0 * nz + z) * zs + q] = pc_a(p[s]);
+        f.S[(size_t)(1 * nz + z) * zs + q] = pc_b(p[s]);
+        f.S[(size_t)(2 * nz + z) * zs + q] = c[s];
+      }
+    }
+    __syncthreads();   // the exchange buffers are written again by the next tile
   }
 }
 
@@ -340,7 +565,7 @@ bool fast_split_supported(int Py, int Pz) { return Py >= 16 && Py <= 2048 && Pz 
 // rows per block (y: two per pair) and columns per z block (zt = 256 or 128 threads)
 int fast_y_rows(int Py) { return 2 * y_pairs(Py); }
 int fast_z_cols(int Pz, int zt) {
-  return zt == kZ16 && Pz == 128 ? kZ16Cols : z_threads(Pz, zt) / (Pz / 8);
+  return (zt == kZ16 || zt == kZ16T) && Pz == 128 ? kZ16Cols : z_threads(Pz, zt) / (Pz / 8);
 }
 size_t fast_y_smem(int Py) { return (size_t)y_pairs(Py) * pk_line_stride(Py) * sizeof(float4); }
 size_t fast_z_smem(int Pz, int zt) {
@@ -355,12 +580,66 @@ cudaError_t configure_fast_split(int Py, int Pz) {
   if (e == cudaSuccess && Pz == 128)
     e = cudaFuncSetAttribute((const void*)kz_fast16, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)fast_z_smem(128, kZ16));
+  if (e == cudaSuccess && Pz == 128)   // the largest depth of a padded z length of 128: nz = 64
+    e = cudaFuncSetAttribute((const void*)kz_tma16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zt_smem(64));
   return e;
 }
 
 cudaError_t launch_fast_y(int Py, int dir, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s) {
   if (nunits <= 0) return cudaSuccess;
   return ydispatch(Py, dir, films, lp, nunits, y_threads(Py), fast_y_smem(Py), s, false);
+}
+
+cudaError_t make_z_map(ZMap* map, float2* S, int ncol, int rows) {
+  static_assert(sizeof(ZMap) == sizeof(CUtensorMap) && alignof(ZMap) >= alignof(CUtensorMap), "tensor map storage");
+  if (rows < 1 || rows > 256 || ncol < kZ16Cols || ncol % kZ16Cols != 0 ||
+      (reinterpret_cast<uintptr_t>(S) & 15) != 0)
+    return cudaErrorInvalidValue;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  // innermost dimension: the ncol columns (8-byte elements, contiguous); outer: the rows
+  // (c, z), ncol * 8 bytes apart (a multiple of 128).  Box: kZ16Cols columns (128 bytes)
+  // by all rows; the column coordinate of every copy is a multiple of kZ16Cols.
+  const cuuint64_t dims[2] = {(cuuint64_t)ncol, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ncol * sizeof(float2)};
+  const cuuint32_t box[2] = {(cuuint32_t)kZ16Cols, (cuuint32_t)rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, S, dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// staged z pass: at most three blocks per SM, each walking its tiles (all co-resident, or
+// in waves when fewer fit: no block waits on another)
+cudaError_t launch_z_tma(const FilmDev* films, const LaunchP& lp, int ntiles, cudaStream_t s, const ZMap* map,
+                         int nz) {
+  const int grid = std::min(ntiles, 3 * std::max(1, lp.nsm));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kZTThreads);
+  cfg.dynamicSmemBytes = zt_smem(nz);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = lp.pdl ? 1 : 0;
+  const CUtensorMap& m = *reinterpret_cast<const CUtensorMap*>(map);
+  return cudaLaunchKernelEx(&cfg, kz_tma16, films, lp, m);
+}
+
+cudaError_t launch_fast_z_tma(const FilmDev* films, const LaunchP& lp, int ntiles, int nz, const ZMap* map,
+                              cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (!map || nz < 1 || 3 * nz > 256) return cudaErrorInvalidValue;
+  return launch_z_tma(films, lp, ntiles, s, map, nz);
 }
 
 cudaError_t launch_fast_z(int Pz, int zt, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s) {

@@ -79,6 +79,12 @@ struct LaunchP {
   const float2* twb; // per-base twiddle tables: exp(-2 pi i k / B) at twb[B - 2 + k], B = 2..GRACE_LMAX
   int pdl;          // launch with programmatic stream serialization
   int xhelp;        // x pass: helper warps on one- and two-warp tiles (few blocks in flight)
+  int nsm;          // SMs of the device: the split passes pull the inputs of the block one
+                    // wave later (its resident blocks per SM x nsm units on) into L2
+  int* status;      // workspace status word: GRACE_ETIMEOUT once a bounded wait ran out
+  unsigned long long limit_ns;   // bound of every wait on a copy or barrier
+  int skip_copy_block;  // failure-detection test hook: this block of the staged z pass skips
+                        // its first copy (-1: none)
   float* k1;        // Heun: f(m_n), concatenated films (3 N)
   const float* hscale;  // applied-field envelope {s(t_n), s(t_n + dt)}, nullptr: constant field
   // adjoint (concatenated films; nullptr when unused)
@@ -182,10 +188,23 @@ int fast_y_rows(int Py);
 // zt: z-pass schedule: 256 or 128 threads per block at 8 points per thread, or kZ16: 16
 // points per thread (Pz = 128 only, one exchange per transform)
 constexpr int kZ16 = 16;
+// kZ16T: the 16-points-per-thread z pass as a persistent kernel whose blocks stage the next
+// tile's spectrum columns into shared memory with a TMA tensor copy (one film per launch)
+constexpr int kZ16T = 18;
+// Opaque storage of a TMA tensor map (CUtensorMap: 128 bytes, 128-byte aligned).
+struct alignas(128) ZMap {
+  unsigned char bytes[128];
+};
+// Tensor map of a film's split-path spectrum S viewed as 3 nz rows of ncol = Kx Py complex
+// values (8 bytes each) with boxes of kZ16 columns by all rows.
+cudaError_t make_z_map(ZMap* map, float2* S, int ncol, int rows);
 int fast_z_cols(int Pz, int zt);
 cudaError_t configure_fast_split(int Py, int Pz);
 cudaError_t launch_fast_y(int Py, int dir, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s);
 cudaError_t launch_fast_z(int Pz, int zt, const FilmDev* films, const LaunchP& lp, int nunits, cudaStream_t s);
+// kZ16T (Pz = 128, one film): ntiles = Kx Py / 16 tiles of the film whose S the map describes
+cudaError_t launch_fast_z_tma(const FilmDev* films, const LaunchP& lp, int ntiles, int nz, const ZMap* map,
+                              cudaStream_t s);
 
 struct TensorJob {
   int nx, ny, nz, Px, Py, Pz, Kx, Ky, Kz, zfft, nslot;

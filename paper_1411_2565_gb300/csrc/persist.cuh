@@ -15,7 +15,7 @@ constexpr int kPersistTimeout = -4;    // status value of an expired barrier wai
 struct PersistSync {
   unsigned count;        // blocks arrived at the current barrier
   unsigned generation;   // barriers completed
-  int status;            // 0, or kPersistTimeout once a wait ran out
+  int status;            // 0, or kPersistTimeout once a wait ran out (also the staged z pass)
   unsigned pad;
 };
 

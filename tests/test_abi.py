@@ -175,7 +175,7 @@ def test_batch_path_options_are_validated_on_the_host(lib):
     assert lib.grace_set_option(ctx, _lib.OPT_TEST_SKIP_ARRIVE, -2) == EINVAL
     assert lib.grace_set_option(ctx, _lib.OPT_TEST_SKIP_ARRIVE, 3) == 0
     assert lib.grace_set_option(ctx, _lib.OPT_TEST_SKIP_ARRIVE, -1) == 0
-    assert lib.grace_set_option(ctx, _lib.OPT_TILE_Z, 4) == EINVAL
+    assert lib.grace_set_option(ctx, _lib.OPT_TILE_Z, 5) == EINVAL
     assert lib.grace_set_option(ctx, _lib.OPT_SIDE_STREAMS, 0) == 0
     assert lib.grace_sync(ctx) == ESTATE
     assert lib.grace_destroy(ctx) == 0

@@ -49,7 +49,7 @@ def test_block_and_ensemble_schedules_match_the_defaults():
     ref = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, tuned=False)
     ref.set_m(md)
     ref.step(3, w.dt)
-    for o in (autotune.best([f]), {_lib.OPT_TILE_Z: 3}, {_lib.OPT_TILE_Z: 0, _lib.OPT_PDL: 0}):
+    for o in (autotune.best([f]), {_lib.OPT_TILE_Z: 3}, {_lib.OPT_TILE_Z: 4}, {_lib.OPT_TILE_Z: 0, _lib.OPT_PDL: 0}):
         g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, options=o)
         g.set_m(md)
         g.step(3, w.dt)

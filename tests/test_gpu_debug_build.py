@@ -1,8 +1,8 @@
 """The checked build (libgrace_debug.so, -DGRACE_DEBUG): the kernels record failed index and
 shared-memory-extent checks in a workspace word instead of trapping, and every runtime
 buffer is followed by a guard region.  Odd and edge shapes that take every launch path
-(runtime-length x / y / z kernels, the fused and the split compile-time paths, a batch on
-the grouped and the persistent launch, Heun, the adjoint on both x passes) must leave the word clear and the guards intact, and give the
+(runtime-length x / y / z kernels, the fused and the split compile-time paths, the staged z
+pass, a batch on the grouped and the persistent launch, Heun, the adjoint on both x passes) must leave the word clear and the guards intact, and give the
 release library's results.
 
 Each library runs in a subprocess of its own (GRACE_DEBUG selects which one the binding
@@ -50,6 +50,15 @@ for grid in shapes:
     arrays["heun%s" % (grid,)] = g.get_m().cpu().numpy()
     check(g, "heun%s" % (grid,))
     g.close()
+# the staged z pass (TMA copies of the spectrum columns) on a padded z length of 128
+f, m0 = workloads.small_film((24, 20, 33), seed=8, Ku=1e4, alpha=0.2, hext=(1e4, -5e3, 2e3))
+g = Grace(f.grid, f.cell, f.Ms, f.A, f.Ku, f.alpha, f.gamma0, options={_lib.OPT_TILE_Z: 4})
+g.set_hext(f.hext)
+g.set_m(torch.from_numpy(m0.reshape(-1)).cuda())
+g.step(5, 1e-14)
+arrays["staged_z"] = g.get_m().cpu().numpy()
+check(g, "staged_z")
+g.close()
 w = workloads.ensemble(nfilms=8, seed=51)
 mb = torch.from_numpy(np.concatenate([m.reshape(-1) for m in w.m0])).cuda()
 for pers in (0, 1):

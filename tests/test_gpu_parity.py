@@ -76,7 +76,7 @@ def test_heff_matches_oracle(grid, mask):
 
 # the z-pass schedules of a padded z length of 128 (16 points per thread, the default there;
 # 128- and 256-thread blocks at 8 points per thread), ragged in every axis
-@pytest.mark.parametrize("tile_z", [0, 1, 2, 3])
+@pytest.mark.parametrize("tile_z", [0, 1, 2, 3, 4])
 def test_z_schedules_match_oracle(tile_z):
     Grace, _ = _grace()
     grid = (11, 13, 41)
