@@ -58,11 +58,13 @@ __host__ __device__ constexpr bool x_helpers(int Q, int TY, int MODE, bool H) {
 __host__ __device__ constexpr int x_threads(int Q, int TY, int MODE, bool H) {
   return x_helpers(Q, TY, MODE, H) ? 4 * (TY * Q / 8) : TY * Q / 8;
 }
-// Resident blocks the register bound aims at: 128-thread tiles 6 (up to 80 registers;
-// measured faster than 4 despite a few spilled bytes), blocks with helpers 512 threads per
-// SM in all, others 2.
+// Resident blocks the register bound aims at: 128-thread tiles 5 (up to 102 registers, no
+// spills; on the 256x256x64 block's x pass 115.0 us at 5, 121.0 at 6 with 80 registers,
+// 118.1 at 4, 132.9 at 7 with 72 registers and spills: the cell update's stencil loads
+// gain from the L1 that fewer blocks' shared memory leaves), blocks with helpers 512
+// threads per SM in all, others 2.
 __host__ __device__ constexpr int x_min_blocks(int Q, int TY, int MODE, bool H) {
-  return x_helpers(Q, TY, MODE, H) ? 512 / x_threads(Q, TY, MODE, H) : (TY * Q / 8 == 128 ? 6 : 2);
+  return x_helpers(Q, TY, MODE, H) ? 512 / x_threads(Q, TY, MODE, H) : (TY * Q / 8 == 128 ? 5 : 2);
 }
 
 // One x-pass tile (work unit `unit`) computed by NTB threads of the block, the first
